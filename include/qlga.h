@@ -1,0 +1,164 @@
+/*
+ * qlga.h — C ABI of the spin-2 BEC quantum lattice gas algorithm (QLGA) library.
+ *
+ * The library advances the 10-qubit-per-site QLGA state of a spin-2 Bose-Einstein
+ * condensate (Taylor, Smith & Yepez, arXiv:1907.12834) on one GPU.  One time step is
+ *
+ *     psi(t + tau) = (I'_1 I'_1 I'_2 I'_2 U) psi(t)            (Sec. VII.B, operator
+ *                                                               product of the plain step)
+ *
+ * with the self-interaction unitary U = exp(-i delta V(psi)) applied first, then the kinetic
+ * blocks I'_c = S_c C S^T_c C along x (and then along y in 2D).
+ *
+ * ---------------------------------------------------------------------------------------
+ * State layout ("qubit-pair planes").  Every state buffer, on the host or on the device,
+ * holds 5 planes, one per Zeeman level m = +2, +1, 0, -1, -2 (in that order).  A plane
+ * holds ny*nx sites, x fastest.  A site holds the two qubit amplitudes of that level
+ * (Sec. IV.B, Eq. full_state: two qubits per m_f) as four reals:
+ *
+ *     a.re, a.im, b.re, b.im        (a = first qubit of the pair, b = second)
+ *
+ * so element (m, y, x, q, c) sits at offset (((m*ny + y)*nx + x)*2 + q)*2 + c.  The reals
+ * are float for precision 32 and double for precision 64.  The boson field of level m is
+ * psi_m = a_m + b_m; a boson field psi loaded with qlga_load_boson() is split as
+ * a = b = eps*psi/2 (Sec. VII.A, Eq. eomscaling: psi_lattice = sqrt(gamma) psi, gamma = eps^2).
+ *
+ * Lattice units: x = eps*j, t = eps^2*n.  Periodic boundaries on every axis.
+ *
+ * Ownership.  qlga_create() allocates the device state and work buffers with cudaMalloc
+ * and qlga_destroy() frees them.  qlga_create_external() uses caller-owned device buffers
+ * instead; the caller keeps them alive until qlga_destroy().  Host buffers always belong to
+ * the caller.
+ *
+ * Streams and threading.  Every call that launches work enqueues it on the handle's CUDA
+ * stream (the one passed at creation; NULL = the legacy default stream).  qlga_step() returns
+ * before the work finishes; qlga_observables(), qlga_get_state() to the host and
+ * qlga_synchronize() wait for the stream.  A handle must not be used from two host threads at
+ * once.
+ *
+ * Errors.  Every call returns a qlga_status and never aborts the process.  After an error,
+ * qlga_last_error() returns a one-line description (per host thread).
+ * ---------------------------------------------------------------------------------------
+ */
+#ifndef QLGA_H
+#define QLGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qlga_status {
+    QLGA_OK = 0,
+    QLGA_ERR_INVALID_ARG = 1,   /* a NULL pointer, a bad size, a bad enum value              */
+    QLGA_ERR_OOM = 2,           /* cudaMalloc failed                                          */
+    QLGA_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed              */
+    QLGA_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (status word set by a kernel) */
+    QLGA_ERR_NOT_FINITE = 5,    /* the state holds NaN or Inf                                 */
+    QLGA_ERR_UNSUPPORTED = 6    /* a valid configuration that this build does not implement   */
+} qlga_status;
+
+/* Where a buffer passed to load/get lives. */
+enum { QLGA_HOST = 0, QLGA_DEVICE = 1 };
+
+/* Collide reading (Sec. VII.B: the collide matrix itself is given in a cited work that the
+ * paper does not reproduce).
+ *   QLGA_KINETIC_K1: I'_c = S_c C S^T_c C with C = 1/2 [[1-i, 1+i], [1+i, 1-i]] (default).
+ *   QLGA_KINETIC_K2: I'_c = S_c C^dagger S^T_c C with C = 1/2 [[1+i, 1-i], [1-i, 1+i]].   */
+enum { QLGA_KINETIC_K1 = 0, QLGA_KINETIC_K2 = 1 };
+
+typedef struct qlga_config {
+    int32_t ndim;            /* 1 or 2                                                       */
+    int32_t precision;       /* 32 (float) or 64 (double)                                    */
+    int64_t nx;              /* sites along x, >= 8                                          */
+    int64_t ny;              /* sites along y, >= 8 for ndim 2; must be 1 for ndim 1         */
+    double g0, g1, g2;       /* density, spin-density and singlet couplings (Sec. II, the
+                                spin-2 interaction Hamiltonian Eq. hamspin2)                 */
+    double epsilon;          /* lattice scaling of Sec. VII.A; used only by qlga_load_boson  */
+    int32_t interleave;      /* 0: plain step (Sec. VII.B).  1: interleaved step, U^(1/4)
+                                (1D) or U^(1/8) (2D) before every kinetic block             */
+    int32_t kinetic_variant; /* QLGA_KINETIC_K1 or QLGA_KINETIC_K2                          */
+} qlga_config;
+
+/* Global observables of the boson field psi = a + b at the current time (FP64 sums).
+ * Sec. IV.A characteristics (Eq. cmap), Sec. IV.C discrete energy (Eq. disecrete_energy). */
+typedef struct qlga_obs {
+    double norm_qubit;        /* sum |a|^2 + |b|^2 over sites and levels (exactly conserved) */
+    double norm_boson;        /* sum |psi|^2                                                 */
+    double pop[5];            /* qubit population of m = +2..-2: sum |a_m|^2 + |b_m|^2       */
+    double magnetisation;     /* sum_m m * pop[m]                                           */
+    double energy;            /* sum over sites of sum_axis sum_m |psi_m(j+1) - psi_m(j)|^2
+                                 + g0/2 rho^2 + g1/2 |F|^2 + g2/10 |psi^T J psi|^2           */
+    double singlet_re;        /* sum psi^T J psi / sqrt(5), (J psi)_m = (-1)^m psi_{-m}       */
+    double singlet_im;
+    double singlet_fraction;  /* sum |psi^T J psi|^2 / sum rho^2                             */
+    double overlap_re;        /* <psi(t) | ref> when a reference state was given, else 0     */
+    double overlap_im;
+    int64_t step;             /* time steps taken since the last load                        */
+} qlga_obs;
+
+typedef struct qlga_handle qlga_handle;
+
+/* Bytes of one state buffer for this configuration (5 * 4 * nx * ny reals). */
+qlga_status qlga_state_bytes(const qlga_config* cfg, size_t* bytes);
+
+/* Bytes of device work memory that qlga_create_external() needs beside the two state
+ * buffers (one more state buffer plus the reduction partials). */
+qlga_status qlga_workspace_bytes(const qlga_config* cfg, size_t* bytes);
+
+/* Validate cfg, allocate the state (two ping-pong buffers) and the workspace on the current
+ * device, and bind the handle to `stream` (a cudaStream_t, may be NULL).  The state starts
+ * at zero.  INVALID_ARG for a bad config, OOM when cudaMalloc fails. */
+qlga_status qlga_create(const qlga_config* cfg, void* stream, qlga_handle** out);
+
+/* Same as qlga_create() but on caller-owned device memory: state0 and state1 each of
+ * qlga_state_bytes(), workspace of at least qlga_workspace_bytes(); all 256-byte aligned.
+ * Nothing is allocated on the device. */
+qlga_status qlga_create_external(const qlga_config* cfg, void* stream, void* state0,
+                                 void* state1, void* workspace, size_t workspace_bytes,
+                                 qlga_handle** out);
+
+/* Load a full 10-amplitude state (layout above, the handle's precision) from host or device
+ * memory.  Resets the step counter.  A host load is a synchronous copy. */
+qlga_status qlga_load_state(qlga_handle* h, const void* src, int where);
+
+/* Load a physical boson field psi (complex, [5][ny][nx], re/im interleaved, the handle's
+ * precision): a = b = epsilon * psi / 2 (Sec. VII.A scaling). */
+qlga_status qlga_load_boson(qlga_handle* h, const void* psi5, int where);
+
+/* Copy the current state (layout above) to host or device memory.  A host copy waits. */
+qlga_status qlga_get_state(qlga_handle* h, void* dst, int where);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+qlga_status qlga_step(qlga_handle* h, int64_t n);
+
+/* Apply only the self-interaction unitary U = exp(-i delta V(psi)) to every site, or only
+ * the kinetic operator (all axes), to the current state.  Stage-wise entry points for
+ * checking the two halves of the step separately (Sec. VII.B). */
+qlga_status qlga_apply_potential(qlga_handle* h, double delta);
+qlga_status qlga_apply_kinetic(qlga_handle* h);
+
+/* Global observables of the current state; waits for the stream.  `ref_state_device` may
+ * be NULL; otherwise it is a device state of the same shape and precision and the overlap
+ * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.C). */
+qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
+
+/* Wait for all work enqueued on the handle's stream. */
+qlga_status qlga_synchronize(qlga_handle* h);
+
+/* Free the handle (and the device memory that qlga_create() allocated).  NULL is OK. */
+qlga_status qlga_destroy(qlga_handle* h);
+
+/* Static description of a status code. */
+const char* qlga_status_string(qlga_status s);
+
+/* One-line description of the last error on this host thread ("" when none). */
+const char* qlga_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLGA_H */

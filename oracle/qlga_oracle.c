@@ -1,0 +1,455 @@
+/*
+ * qlga_oracle.c -- plain, slow FP64 CPU reference ("oracle") of the spin-2 BEC quantum
+ * lattice gas algorithm of Taylor, Smith & Yepez, arXiv:1907.12834.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library calls this file.  It is used by the
+ * tests, by the smoke check and by the CPU-baseline leg of the benchmark, and it shares no
+ * code, header or constant with the CUDA path.  Every step is written the plain way the
+ * paper states it: whole-lattice sweeps, one operator at a time, FP64 complex arithmetic,
+ * and the self-interaction unitary taken from a Hermitian eigendecomposition.
+ *
+ * State layout (same as the library's data format): 5 planes m = +2..-2, each ny*nx sites
+ * with x fastest, each site (a.re, a.im, b.re, b.im): element (m, site, q, c) at
+ * ((m*nsites + site)*2 + q)*2 + c.  a = qubit 1 of the pair, b = qubit 2 (Sec. IV.B, Eq.
+ * full_state: two qubits per m_f level).
+ *
+ * Readings of passages the paper leaves open (the same ones the library documents):
+ *  - boson field of level m: psi_m = a_m + b_m;
+ *  - potential V(psi) = g0 rho 1 + g1 sum_nu F_nu f_nu + (g2/5) s s^dagger with
+ *    F_nu = psi^dagger f_nu psi and s_m = (-1)^m conj(psi_{-m}); this is the right-hand
+ *    side of Eq. eomspin2 / eom_component_form written as V(psi) psi, with the singlet
+ *    factor of Eq. spinsinglet read as psi^T J psi / 5 (the printed |A00|^2 and the dropped
+ *    (-1)^m are typesetting slips: every row of Table I is an eigenvector of this V);
+ *  - U = exp(-i delta V(psi)) with V frozen at the current psi, applied to a and to b;
+ *  - collide K1: C = 1/2 [[1-i, 1+i], [1+i, 1-i]], block I'_c = S_c C S^T_c C;
+ *    collide K2: C = 1/2 [[1+i, 1-i], [1-i, 1+i]], block I'_c = S_c C^dagger S^T_c C;
+ *  - S_c moves qubit c one site toward +x: c(j) <- c(j-1); S^T_c the other way;
+ *  - one axis of the kinetic operator is I'_1 I'_1 I'_2 I'_2 (Sec. VII.B), so the I'_2
+ *    blocks act first; in 2D the x axis acts before the y axis.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+typedef struct oracle_cfg {
+    int ndim;              /* 1 or 2 */
+    long nx, ny;           /* ny == 1 in 1D */
+    double g0, g1, g2;     /* couplings of Eq. hamspin2 */
+    int interleave;        /* 0 plain step, 1 interleaved step (Sec. VII.B) */
+    int kinetic_variant;   /* 0 = K1, 1 = K2 */
+} oracle_cfg;
+
+/* ---------------------------------------------------------------- element access */
+
+static inline double* amp(double* s, long nsites, int m, long site, int q) {
+    return s + ((m * nsites + site) * 2 + q) * 2;
+}
+static inline cplx getc(const double* p) { return p[0] + I * p[1]; }
+static inline void putc_(double* p, cplx z) { p[0] = creal(z); p[1] = cimag(z); }
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+/* ---------------------------------------------------------------- spin-2 matrices */
+
+/* f_x, f_y, f_z of Sec. II (the spin-2 SU(2) representation, hbar = 1), rows/columns
+ * ordered m = +2..-2. */
+static void spin2_matrices(cplx fx[5][5], cplx fy[5][5], cplx fz[5][5]) {
+    const double r = sqrt(1.5);
+    memset(fx, 0, sizeof(cplx) * 25);
+    memset(fy, 0, sizeof(cplx) * 25);
+    memset(fz, 0, sizeof(cplx) * 25);
+    const double off[4] = {1.0, r, r, 1.0};
+    for (int i = 0; i < 4; ++i) {
+        fx[i][i + 1] = off[i];
+        fx[i + 1][i] = off[i];
+        fy[i][i + 1] = -I * off[i];
+        fy[i + 1][i] = I * off[i];
+    }
+    for (int i = 0; i < 5; ++i) fz[i][i] = 2.0 - i;
+}
+
+/* V(psi) of Eq. eomspin2 (see the readings above). */
+static void potential_matrix(const cplx psi[5], double g0, double g1, double g2, cplx V[5][5]) {
+    cplx fx[5][5], fy[5][5], fz[5][5];
+    spin2_matrices(fx, fy, fz);
+    double rho = 0.0;
+    for (int i = 0; i < 5; ++i) rho += creal(conj(psi[i]) * psi[i]);
+    double F[3] = {0.0, 0.0, 0.0};
+    cplx (*f[3])[5] = {fx, fy, fz};
+    for (int nu = 0; nu < 3; ++nu) {
+        cplx acc = 0.0;
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) acc += conj(psi[i]) * f[nu][i][j] * psi[j];
+        F[nu] = creal(acc);
+    }
+    cplx s[5];
+    for (int i = 0; i < 5; ++i) {
+        const int m = 2 - i;
+        const double sign = (m % 2 == 0) ? 1.0 : -1.0;
+        s[i] = sign * conj(psi[4 - i]); /* psi_{-m} sits at position 4 - i */
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            cplx v = (i == j) ? g0 * rho : 0.0;
+            for (int nu = 0; nu < 3; ++nu) v += g1 * F[nu] * f[nu][i][j];
+            v += (g2 / 5.0) * s[i] * conj(s[j]);
+            V[i][j] = v;
+        }
+}
+
+/* ------------------------------------------------ Hermitian eigendecomposition (Jacobi)
+ *
+ * Cyclic Jacobi method for a complex Hermitian matrix.  Each rotation zeroes A[p][q]:
+ * with A[p][q] = r e^{i phi}, D = diag(1, e^{-i phi}) on (p, q) makes the pair real, and
+ * the real rotation R = [[c, s], [-s, c]] with t = tan(theta) the smaller root of
+ * t^2 + 2 tau t - 1 = 0, tau = (A[q][q] - A[p][p]) / (2 r), diagonalises it.  G = D R,
+ * A <- G^H A G, Q <- Q G.  On exit A is diagonal (eigenvalues) and the columns of Q are
+ * orthonormal eigenvectors.
+ */
+static void herm_eig(cplx A[5][5], double lam[5], cplx Q[5][5]) {
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) Q[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                const double a2 = creal(A[i][j] * conj(A[i][j]));
+                tot += a2;
+                if (i != j) off += a2;
+            }
+        if (off == 0.0 || off <= 1e-36 * tot) break;
+        for (int p = 0; p < 4; ++p)
+            for (int q = p + 1; q < 5; ++q) {
+                const double r = cabs(A[p][q]);
+                if (r == 0.0) continue;
+                const cplx u = A[p][q] / r;
+                const double tau = (creal(A[q][q]) - creal(A[p][p])) / (2.0 * r);
+                const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                const double c = 1.0 / sqrt(1.0 + t * t);
+                const double s = t * c;
+                const cplx Gpp = c, Gpq = s, Gqp = -s * conj(u), Gqq = c * conj(u);
+                for (int k = 0; k < 5; ++k) { /* columns: A <- A G */
+                    const cplx akp = A[k][p], akq = A[k][q];
+                    A[k][p] = akp * Gpp + akq * Gqp;
+                    A[k][q] = akp * Gpq + akq * Gqq;
+                    const cplx qkp = Q[k][p], qkq = Q[k][q];
+                    Q[k][p] = qkp * Gpp + qkq * Gqp;
+                    Q[k][q] = qkp * Gpq + qkq * Gqq;
+                }
+                for (int k = 0; k < 5; ++k) { /* rows: A <- G^H A */
+                    const cplx apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = conj(Gpp) * apk + conj(Gqp) * aqk;
+                    A[q][k] = conj(Gpq) * apk + conj(Gqq) * aqk;
+                }
+                A[p][q] = 0.0;
+                A[q][p] = 0.0;
+                A[p][p] = creal(A[p][p]);
+                A[q][q] = creal(A[q][q]);
+            }
+    }
+    for (int i = 0; i < 5; ++i) lam[i] = creal(A[i][i]);
+}
+
+/* U = exp(-i delta V) = sum_k e^{-i delta lambda_k} v_k v_k^dagger (spectral theorem). */
+static void expm_herm(const cplx V[5][5], double delta, cplx U[5][5]) {
+    cplx A[5][5], Q[5][5];
+    double lam[5];
+    memcpy(A, V, sizeof(A));
+    herm_eig(A, lam, Q);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += Q[i][k] * cexp(-I * delta * lam[k]) * conj(Q[j][k]);
+            U[i][j] = acc;
+        }
+}
+
+/* ---------------------------------------------------------------- potential step */
+
+/* U = exp(-i delta V(psi)) at every site, psi = a + b, applied to the 5-vector a and to the
+ * 5-vector b (Sec. VII.B; the operator itself is the plain-step factor U, or U^(1/4),
+ * U^(1/8) of the interleaved step through delta). */
+static void apply_potential(double* st, const oracle_cfg* cfg, double delta) {
+    const long n = cfg->nx * cfg->ny;
+#pragma omp parallel for schedule(static)
+    for (long site = 0; site < n; ++site) {
+        cplx a[5], b[5], psi[5], V[5][5], U[5][5];
+        for (int m = 0; m < 5; ++m) {
+            a[m] = getc(amp(st, n, m, site, 0));
+            b[m] = getc(amp(st, n, m, site, 1));
+            psi[m] = a[m] + b[m];
+        }
+        potential_matrix(psi, cfg->g0, cfg->g1, cfg->g2, V);
+        expm_herm(V, delta, U);
+        for (int i = 0; i < 5; ++i) {
+            cplx ua = 0.0, ub = 0.0;
+            for (int j = 0; j < 5; ++j) {
+                ua += U[i][j] * a[j];
+                ub += U[i][j] * b[j];
+            }
+            putc_(amp(st, n, i, site, 0), ua);
+            putc_(amp(st, n, i, site, 1), ub);
+        }
+    }
+}
+
+/* ---------------------------------------------------------------- kinetic operator */
+
+/* The 2x2 collide on every qubit pair (a_m, b_m).  which = 0: the collide C of the
+ * variant; which = 1: the second collide of a block (C for K1, C^dagger for K2). */
+static void collide(double* st, const oracle_cfg* cfg, int which) {
+    const long n = cfg->nx * cfg->ny;
+    cplx C[2][2];
+    if (cfg->kinetic_variant == 0 || which == 1) {
+        C[0][0] = 0.5 * (1.0 - I); C[0][1] = 0.5 * (1.0 + I);
+        C[1][0] = 0.5 * (1.0 + I); C[1][1] = 0.5 * (1.0 - I);
+    } else {
+        C[0][0] = 0.5 * (1.0 + I); C[0][1] = 0.5 * (1.0 - I);
+        C[1][0] = 0.5 * (1.0 - I); C[1][1] = 0.5 * (1.0 + I);
+    }
+    /* K1 uses C twice; K2 uses C then C^dagger, and C_K2^dagger equals C_K1. */
+#pragma omp parallel for schedule(static)
+    for (long site = 0; site < n; ++site)
+        for (int m = 0; m < 5; ++m) {
+            double* pa = amp(st, n, m, site, 0);
+            double* pb = amp(st, n, m, site, 1);
+            const cplx a = getc(pa), b = getc(pb);
+            putc_(pa, C[0][0] * a + C[0][1] * b);
+            putc_(pb, C[1][0] * a + C[1][1] * b);
+        }
+}
+
+/* Stream qubit q of every level one site along `axis` (0 = x, 1 = y):
+ * dir = +1 is S_q, q(j) <- q(j-1); dir = -1 is S^T_q, q(j) <- q(j+1).  Periodic. */
+static void stream(double* st, const oracle_cfg* cfg, int axis, int q, int dir) {
+    const long nx = cfg->nx, ny = cfg->ny, n = nx * ny;
+    cplx* tmp = (cplx*)malloc(sizeof(cplx) * n);
+    for (int m = 0; m < 5; ++m) {
+        for (long site = 0; site < n; ++site) tmp[site] = getc(amp(st, n, m, site, q));
+#pragma omp parallel for schedule(static)
+        for (long y = 0; y < ny; ++y)
+            for (long x = 0; x < nx; ++x) {
+                long sx = x, sy = y;
+                if (axis == 0) sx = ((x - dir) % nx + nx) % nx;
+                else sy = ((y - dir) % ny + ny) % ny;
+                putc_(amp(st, n, m, y * nx + x, q), tmp[sy * nx + sx]);
+            }
+    }
+    free(tmp);
+}
+
+/* One kinetic block I'_c = S_c C S^T_c C along `axis` for qubit c = q (operators act
+ * right to left). */
+static void kinetic_block(double* st, const oracle_cfg* cfg, int axis, int q) {
+    collide(st, cfg, 0);
+    stream(st, cfg, axis, q, -1);
+    collide(st, cfg, 1);
+    stream(st, cfg, axis, q, +1);
+}
+
+/* Block order on one axis: I'_1 I'_1 I'_2 I'_2 acting on psi, i.e. qubit 2 (b) twice, then
+ * qubit 1 (a) twice. */
+static const int block_qubit[4] = {1, 1, 0, 0};
+
+static void apply_kinetic(double* st, const oracle_cfg* cfg) {
+    for (int axis = 0; axis < cfg->ndim; ++axis)
+        for (int k = 0; k < 4; ++k) kinetic_block(st, cfg, axis, block_qubit[k]);
+}
+
+/* ---------------------------------------------------------------- the time step */
+
+/* Plain step psi(t+1) = K U psi(t); interleaved step: U^(1/4) (1D) or U^(1/8) (2D) before
+ * every kinetic block, in the product order of the interleaved formula of Sec. VII.B. */
+static void step_once(double* st, const oracle_cfg* cfg) {
+    if (!cfg->interleave) {
+        apply_potential(st, cfg, 1.0);
+        apply_kinetic(st, cfg);
+        return;
+    }
+    const double frac = 1.0 / (4.0 * cfg->ndim);
+    for (int axis = 0; axis < cfg->ndim; ++axis)
+        for (int k = 0; k < 4; ++k) {
+            apply_potential(st, cfg, frac);
+            kinetic_block(st, cfg, axis, block_qubit[k]);
+        }
+}
+
+/* ---------------------------------------------------------------- observables */
+
+/* Sums over the lattice of the boson field psi = a + b (Sec. IV.A Eq. cmap, Sec. IV.C Eq.
+ * disecrete_energy); out[] order:
+ *  0 norm_qubit  1 norm_boson  2..6 pop[m=+2..-2]  7 magnetisation  8 energy
+ *  9 singlet_re  10 singlet_im  11 sum |psi^T J psi|^2  12 sum rho^2
+ *  13 overlap_re  14 overlap_im
+ * Energy density: sum_axis sum_m |psi_m(j+1) - psi_m(j)|^2 + g0/2 rho^2 + g1/2 |F|^2
+ * + g2/10 |psi^T J psi|^2 (the functional whose variation gives V(psi) psi). */
+static void observables(const double* st, const double* ref, const oracle_cfg* cfg,
+                        double out[15]) {
+    const long nx = cfg->nx, ny = cfg->ny, n = nx * ny;
+    cplx fx[5][5], fy[5][5], fz[5][5];
+    spin2_matrices(fx, fy, fz);
+    for (int k = 0; k < 15; ++k) out[k] = 0.0;
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            const long site = y * nx + x;
+            cplx psi[5];
+            for (int m = 0; m < 5; ++m) {
+                const cplx a = getc(amp((double*)st, n, m, site, 0));
+                const cplx b = getc(amp((double*)st, n, m, site, 1));
+                psi[m] = a + b;
+                const double pm = creal(conj(a) * a) + creal(conj(b) * b);
+                out[0] += pm;
+                out[2 + m] += pm;
+                out[7] += (2 - m) * pm;
+            }
+            double rho = 0.0;
+            for (int m = 0; m < 5; ++m) rho += creal(conj(psi[m]) * psi[m]);
+            out[1] += rho;
+            double F2 = 0.0;
+            cplx (*f[3])[5] = {fx, fy, fz};
+            for (int nu = 0; nu < 3; ++nu) {
+                cplx acc = 0.0;
+                for (int i = 0; i < 5; ++i)
+                    for (int j = 0; j < 5; ++j) acc += conj(psi[i]) * f[nu][i][j] * psi[j];
+                F2 += creal(acc) * creal(acc);
+            }
+            cplx theta = 0.0; /* psi^T J psi = sum_m (-1)^m psi_m psi_{-m} */
+            for (int i = 0; i < 5; ++i) {
+                const int m = 2 - i;
+                theta += ((m % 2 == 0) ? 1.0 : -1.0) * psi[i] * psi[4 - i];
+            }
+            const double th2 = creal(theta * conj(theta));
+            double grad = 0.0;
+            for (int axis = 0; axis < cfg->ndim; ++axis) {
+                const long xn = axis == 0 ? (x + 1) % nx : x;
+                const long yn = axis == 1 ? (y + 1) % ny : y;
+                const long sn = yn * nx + xn;
+                for (int m = 0; m < 5; ++m) {
+                    const cplx pn = getc(amp((double*)st, n, m, sn, 0)) + getc(amp((double*)st, n, m, sn, 1));
+                    const cplx d = pn - psi[m];
+                    grad += creal(conj(d) * d);
+                }
+            }
+            out[8] += grad + 0.5 * cfg->g0 * rho * rho + 0.5 * cfg->g1 * F2 + 0.1 * cfg->g2 * th2;
+            out[9] += creal(theta) / sqrt(5.0);
+            out[10] += cimag(theta) / sqrt(5.0);
+            out[11] += th2;
+            out[12] += rho * rho;
+            if (ref) {
+                for (int m = 0; m < 5; ++m) {
+                    const cplx r = getc(amp((double*)ref, n, m, site, 0)) + getc(amp((double*)ref, n, m, site, 1));
+                    const cplx ov = conj(psi[m]) * r;
+                    out[13] += creal(ov);
+                    out[14] += cimag(ov);
+                }
+            }
+        }
+}
+
+/* ---------------------------------------------------------------- exported entry points */
+
+static int cfg_ok(const oracle_cfg* cfg) {
+    if (!cfg) return 0;
+    if (cfg->ndim != 1 && cfg->ndim != 2) return 0;
+    if (cfg->nx < 1 || cfg->ny < 1) return 0;
+    if (cfg->ndim == 1 && cfg->ny != 1) return 0;
+    return 1;
+}
+
+int oracle_step(double* state, const oracle_cfg* cfg, long nsteps, int nthreads) {
+    if (!cfg_ok(cfg) || !state || nsteps < 0) return 1;
+    set_threads(nthreads);
+    for (long s = 0; s < nsteps; ++s) step_once(state, cfg);
+    return 0;
+}
+
+int oracle_apply_potential(double* state, const oracle_cfg* cfg, double delta, int nthreads) {
+    if (!cfg_ok(cfg) || !state) return 1;
+    set_threads(nthreads);
+    apply_potential(state, cfg, delta);
+    return 0;
+}
+
+int oracle_apply_kinetic(double* state, const oracle_cfg* cfg, int nthreads) {
+    if (!cfg_ok(cfg) || !state) return 1;
+    set_threads(nthreads);
+    apply_kinetic(state, cfg);
+    return 0;
+}
+
+/* Single operators for the tests: which = 0 collide C, 1 second collide, 2 stream. */
+int oracle_apply_operator(double* state, const oracle_cfg* cfg, int which, int axis, int q,
+                          int dir) {
+    if (!cfg_ok(cfg) || !state) return 1;
+    if (which == 0 || which == 1) collide(state, cfg, which);
+    else if (which == 2) stream(state, cfg, axis, q, dir);
+    else return 1;
+    return 0;
+}
+
+int oracle_observables(const double* state, const double* ref, const oracle_cfg* cfg,
+                       double* out15) {
+    if (!cfg_ok(cfg) || !state || !out15) return 1;
+    observables(state, ref, cfg, out15);
+    return 0;
+}
+
+/* psi10 = (re, im) of psi_{+2..-2}; V50 = 5x5 complex row-major (re, im). */
+int oracle_potential_matrix(const double* psi10, double g0, double g1, double g2, double* V50) {
+    cplx psi[5], V[5][5];
+    for (int i = 0; i < 5; ++i) psi[i] = psi10[2 * i] + I * psi10[2 * i + 1];
+    potential_matrix(psi, g0, g1, g2, V);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            V50[2 * (5 * i + j)] = creal(V[i][j]);
+            V50[2 * (5 * i + j) + 1] = cimag(V[i][j]);
+        }
+    return 0;
+}
+
+/* Hermitian eigendecomposition of V50: lam5 ascending order not guaranteed; Q50 columns. */
+int oracle_heig(const double* V50, double* lam5, double* Q50) {
+    cplx A[5][5], Q[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) A[i][j] = V50[2 * (5 * i + j)] + I * V50[2 * (5 * i + j) + 1];
+    herm_eig(A, lam5, Q);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            Q50[2 * (5 * i + j)] = creal(Q[i][j]);
+            Q50[2 * (5 * i + j) + 1] = cimag(Q[i][j]);
+        }
+    return 0;
+}
+
+int oracle_expm(const double* V50, double delta, double* U50) {
+    cplx V[5][5], U[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) V[i][j] = V50[2 * (5 * i + j)] + I * V50[2 * (5 * i + j) + 1];
+    expm_herm(V, delta, U);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            U50[2 * (5 * i + j)] = creal(U[i][j]);
+            U50[2 * (5 * i + j) + 1] = cimag(U[i][j]);
+        }
+    return 0;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

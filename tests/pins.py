@@ -1,0 +1,275 @@
+"""Pins of the CPU oracle: checks against what the paper and the mathematics fix.
+
+Each function takes an ``oracle.Oracle`` and returns the largest deviation it finds, so the
+same check serves the pin tests (deviation below tolerance) and the mutation tests (a
+planted mistake in a copy of the oracle source pushes it above).
+"""
+import numpy as np
+import scipy.linalg as sl
+
+import oracle
+import golden
+
+# (E, g0, g1, g2) sets; the last one is the bright-soliton case of the 1D configurations
+COUPLING_SETS = [(1.0, 1.0, 0.1, 1.0), (2.0, 1.3, 0.4, 0.7), (1.0, 1.0, 0.3, -0.5),
+                 (-2.0, 1.0, -0.5, 0.2)]
+
+C_K1 = 0.5 * np.array([[1 - 1j, 1 + 1j], [1 + 1j, 1 - 1j]])
+C_K2 = 0.5 * np.array([[1 + 1j, 1 - 1j], [1 - 1j, 1 + 1j]])
+
+
+def collide_pair(variant):
+    """(first, second) collide of a kinetic block: K1 = (C, C), K2 = (C, C^dagger)."""
+    if variant == 0:
+        return C_K1, C_K1
+    return C_K2, C_K2.conj().T
+
+
+# ----------------------------------------------------------------- potential (Table I / II)
+
+def pin_table1(orc):
+    """max |V(c) c - E c| over every real Table I row and coupling set (Sec. III.A)."""
+    worst, count = 0.0, 0
+    for E, g0, g1, g2 in COUPLING_SETS:
+        for row, c in golden.table1(E, g0, g1, g2).items():
+            c = np.asarray(c, dtype=complex)
+            V = orc.potential_matrix(c, g0, g1, g2)
+            worst = max(worst, float(np.abs(V @ c - E * c).max()) / max(1.0, abs(E)))
+            count += 1
+    assert count >= 40
+    return worst
+
+
+def pin_table2(orc):
+    """max deviation from Table II (Sec. IV.A): F_par and F_perp read off V(c) at couplings
+    (0, 1, 0), where V = F.f, and |A00| from the oracle's singlet sum on a one-site lattice.
+    Entries flagged as misprints are skipped."""
+    worst = 0.0
+    for E, g0, g1, g2 in COUPLING_SETS[:3]:
+        rows1 = golden.table1(E, g0, g1, g2)
+        for row, ((fpar, fperp, a00), flags) in golden.table2(E, g0, g1, g2).items():
+            if row not in rows1:
+                continue
+            c = np.asarray(rows1[row], dtype=complex)
+            V = orc.potential_matrix(c, 0.0, 1.0, 0.0)
+            worst = max(worst, abs(abs(V[0, 0].real / 2.0) - fpar))     # f_z[+2,+2] = 2
+            if "perp-misprint" not in flags:
+                worst = max(worst, abs(abs(V[1, 0]) - fperp))          # c_0 = 1: V[1,0] = F_+
+            cfg = oracle.make_cfg(1, 1, 1, g0, g1, g2)
+            st = np.zeros((5, 1, 1, 2, 2))
+            st[:, 0, 0, 0, 0] = st[:, 0, 0, 1, 0] = c.real / 2.0
+            obs = orc.observables(st, cfg)
+            worst = max(worst, abs(abs(complex(obs["singlet_re"], obs["singlet_im"])) - a00))
+    return worst
+
+
+# ----------------------------------------------------------------- exponential
+
+def pin_expm(orc, trials=20):
+    """exp(-i delta V) against scipy.linalg.expm, plus unitarity and the eigen-reconstruction."""
+    rng = np.random.default_rng(7)
+    worst = 0.0
+    for t in range(trials):
+        A = rng.normal(size=(5, 5)) + 1j * rng.normal(size=(5, 5))
+        V = (A + A.conj().T) * (0.05 if t % 2 else 1.0)
+        if t == 3:                                   # degenerate spectrum
+            V = np.diag([0.3, 0.3, -0.1, -0.1, 0.3]).astype(complex)
+        delta = [1.0, 0.25, 0.125, 2.0][t % 4]
+        U = orc.expm(V, delta)
+        worst = max(worst, float(np.abs(U - sl.expm(-1j * delta * V)).max()))
+        worst = max(worst, float(np.abs(U @ U.conj().T - np.eye(5)).max()))
+        lam, Q = orc.heig(V)
+        worst = max(worst, float(np.abs(Q @ np.diag(lam) @ Q.conj().T - V).max()))
+    return worst
+
+
+# ----------------------------------------------------------------- kinetic operator
+
+def kinetic_symbol(kx, ky=None, variant=0):
+    """Fourier symbol (2x2, acting on (a_m, b_m)) of the kinetic operator for a plane wave
+    e^{i(kx x + ky y)}: S_q (q(j) <- q(j-1)) multiplies qubit q by e^{-ik}, S^T_q by e^{+ik};
+    block I'_q = S_q C' S^T_q C; one axis is I'_1 I'_1 I'_2 I'_2 (Sec. VII.B)."""
+    first, second = collide_pair(variant)
+
+    def axis(k):
+        def S(q, d):
+            M = np.eye(2, dtype=complex)
+            M[q, q] = np.exp(-1j * d * k)
+            return M
+
+        def block(q):
+            return S(q, +1) @ second @ S(q, -1) @ first
+        return block(0) @ block(0) @ block(1) @ block(1)
+    K = axis(kx)
+    if ky is not None:
+        K = axis(ky) @ K
+    return K
+
+
+def pin_plane_wave_symbol(orc, variant=0):
+    """The oracle's kinetic operator on every plane wave of a small 1D and 2D lattice equals
+    the closed-form symbol product."""
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    L = 12
+    for n in range(L):
+        k = 2 * np.pi * n / L
+        A = rng.normal(size=(5, 2)) + 1j * rng.normal(size=(5, 2))
+        j = np.arange(L)
+        field = A[:, None, None, :] * np.exp(1j * k * j)[None, None, :, None]
+        st = np.stack([field.real, field.imag], axis=-1).copy()
+        cfg = oracle.make_cfg(1, L, 1, 0, 0, 0, kinetic_variant=variant)
+        orc.apply_kinetic(st, cfg)
+        got = st[..., 0] + 1j * st[..., 1]
+        want = (A @ kinetic_symbol(k, variant=variant).T)[:, None, None, :] * \
+            np.exp(1j * k * j)[None, None, :, None]
+        worst = max(worst, float(np.abs(got - want).max()))
+    nx, ny = 6, 5
+    for nxw in range(nx):
+        for nyw in range(ny):
+            kx, ky = 2 * np.pi * nxw / nx, 2 * np.pi * nyw / ny
+            A = rng.normal(size=(5, 2)) + 1j * rng.normal(size=(5, 2))
+            ph = np.exp(1j * (kx * np.arange(nx)[None, :] + ky * np.arange(ny)[:, None]))
+            field = A[:, None, None, :] * ph[None, :, :, None]
+            st = np.stack([field.real, field.imag], axis=-1).copy()
+            cfg = oracle.make_cfg(2, nx, ny, 0, 0, 0, kinetic_variant=variant)
+            orc.apply_kinetic(st, cfg)
+            got = st[..., 0] + 1j * st[..., 1]
+            want = (A @ kinetic_symbol(kx, ky, variant=variant).T)[:, None, None, :] * \
+                ph[None, :, :, None]
+            worst = max(worst, float(np.abs(got - want).max()))
+    return worst
+
+
+def kinetic_phase_error(orc, variant=0, L=2048):
+    """Sec. VII.B: the kinetic operator is psi - i p^2 psi + O(p^4) on the boson (a = b)
+    mode.  Returns max over small kappa of |(<s|K s> - 1)/kappa^2 + i| / kappa^2."""
+    worst = 0.0
+    for n in (1, 2, 4, 8):
+        k = 2 * np.pi * n / L
+        j = np.arange(L)
+        w = np.exp(1j * k * j)
+        st = np.zeros((5, 1, L, 2, 2))
+        for q in (0, 1):
+            st[2, 0, :, q, 0] = w.real / np.sqrt(2)
+            st[2, 0, :, q, 1] = w.imag / np.sqrt(2)
+        cfg = oracle.make_cfg(1, L, 1, 0, 0, 0, kinetic_variant=variant)
+        orc.apply_kinetic(st, cfg)
+        a = st[2, 0, :, 0, 0] + 1j * st[2, 0, :, 0, 1]
+        b = st[2, 0, :, 1, 0] + 1j * st[2, 0, :, 1, 1]
+        amp = np.mean((a + b) / np.sqrt(2) * np.conj(w))        # <s| K |s> for the plane wave
+        worst = max(worst, abs((amp - 1.0) / k ** 2 + 1j) / k ** 2)
+    return worst
+
+
+# ----------------------------------------------------------------- dense brute force
+
+def _vec(st):
+    return (st[..., 0] + 1j * st[..., 1]).reshape(-1)
+
+
+def _unvec(v, shape):
+    z = v.reshape(shape[:-1])
+    return np.stack([z.real, z.imag], axis=-1)
+
+
+def dense_collide(N, C):
+    D = np.zeros((10 * N, 10 * N), dtype=complex)
+    for m in range(5):
+        for s in range(N):
+            i0 = (m * N + s) * 2
+            D[i0:i0 + 2, i0:i0 + 2] = C
+    return D
+
+
+def dense_stream(nx, ny, axis, q, d):
+    """Permutation: qubit q of every level moves one site toward +axis (d=+1) or -axis."""
+    N = nx * ny
+    P = np.zeros((10 * N, 10 * N))
+    for m in range(5):
+        for y in range(ny):
+            for x in range(nx):
+                s = y * nx + x
+                for qq in (0, 1):
+                    if qq == q:
+                        sx, sy = ((x - d) % nx, y) if axis == 0 else (x, (y - d) % ny)
+                    else:
+                        sx, sy = x, y
+                    P[(m * N + s) * 2 + qq, (m * N + sy * nx + sx) * 2 + qq] = 1.0
+    return P
+
+
+def dense_potential(orc, v, N, g, delta):
+    """Block-diagonal U = exp(-i delta V(psi_site)) acting on the level index of each qubit;
+    V from the (Table I-pinned) oracle matrix, the exponential from scipy."""
+    z = v.reshape(5, N, 2)
+    D = np.zeros((10 * N, 10 * N), dtype=complex)
+    for s in range(N):
+        psi = z[:, s, 0] + z[:, s, 1]
+        Us = sl.expm(-1j * delta * orc.potential_matrix(psi, *g))
+        for q in (0, 1):
+            idx = [(m * N + s) * 2 + q for m in range(5)]
+            D[np.ix_(idx, idx)] = Us
+    return D
+
+
+def pin_dense_step(orc, ndim, interleave=0, variant=0, nsteps=2, seed=3):
+    """One oracle step against the product of dense operator matrices on a tiny lattice
+    (L = 4 in 1D, 3 x 3 in 2D) with random amplitudes and couplings."""
+    rng = np.random.default_rng(seed)
+    nx, ny = (4, 1) if ndim == 1 else (3, 3)
+    N = nx * ny
+    g = tuple(rng.uniform(-1, 1, size=3))
+    st = 0.3 * rng.normal(size=(5, ny, nx, 2, 2))
+    cfg = oracle.make_cfg(ndim, nx, ny, *g, interleave=interleave, kinetic_variant=variant)
+    first, second = collide_pair(variant)
+    C1, C2 = dense_collide(N, first), dense_collide(N, second)
+    v = _vec(st)
+    for _ in range(nsteps):
+        blocks = []
+        for axis in range(ndim):
+            for q in (1, 1, 0, 0):
+                blocks.append(dense_stream(nx, ny, axis, q, +1) @ C2 @
+                              dense_stream(nx, ny, axis, q, -1) @ C1)
+        if not interleave:
+            v = dense_potential(orc, v, N, g, 1.0) @ v
+            for B in blocks:
+                v = B @ v
+        else:
+            for B in blocks:
+                v = dense_potential(orc, v, N, g, 1.0 / (4 * ndim)) @ v
+                v = B @ v
+    orc.step(st, cfg, nsteps)
+    return float(np.abs(_vec(st) - v).max())
+
+
+# ----------------------------------------------------------------- exact Thomas-Fermi phase
+
+def pin_tf_phase(orc, interleave=0, nsteps=3):
+    """A uniform Table I state with a = b = c/2 is an exact eigenvector of one QLGA step:
+    the kinetic operator is the identity on it (zero wavenumber, a = b) and V(c) c = E c, so
+    n steps multiply it by exp(-i E n) exactly."""
+    worst = 0.0
+    for E, g0, g1, g2 in COUPLING_SETS[:3]:
+        Elat = 0.02 * E                   # lattice energy: small field, as after eps-scaling
+        for row, c in golden.table1(Elat, g0, g1, g2, c1=0.03, c2=0.02).items():
+            c = np.asarray(c)
+            for ndim, (nx, ny) in ((1, (8, 1)), (2, (4, 3))):
+                st = np.zeros((5, ny, nx, 2, 2))
+                st[..., 0, 0] = st[..., 1, 0] = (c / 2.0)[:, None, None]
+                want = np.exp(-1j * Elat * nsteps) * _vec(st)
+                cfg = oracle.make_cfg(ndim, nx, ny, g0, g1, g2, interleave=interleave)
+                orc.step(st, cfg, nsteps)
+                worst = max(worst, float(np.abs(_vec(st) - want).max()) / max(np.abs(c).max(), 1e-300))
+    return worst
+
+
+def pin_norm(orc, ndim=2, nsteps=4):
+    """Unitarity: the qubit norm after nsteps of a random state, relative drift."""
+    rng = np.random.default_rng(5)
+    nx, ny = (7, 1) if ndim == 1 else (6, 5)
+    st = 0.2 * rng.normal(size=(5, ny, nx, 2, 2))
+    cfg = oracle.make_cfg(ndim, nx, ny, 1.0, 0.8, -0.6)
+    n0 = float((st ** 2).sum())
+    orc.step(st, cfg, nsteps)
+    return abs(float((st ** 2).sum()) - n0) / n0

@@ -1,0 +1,43 @@
+"""Plant a plausible mistake in a copy of the oracle source and check that a pin catches it.
+
+Each case edits one line of the oracle (a dropped sign, a flipped exponent, a reversed
+stream, a reordered block, a halved term, a conjugation slip), compiles the copy with gcc
+and runs the pin that should fail.  The real oracle is never modified.
+"""
+import pytest
+
+import oracle
+import pins
+
+MUTATIONS = [
+    # (id, original text, replacement, pin that must fail, its pass threshold)
+    ("singlet_sign", "const double sign = (m % 2 == 0) ? 1.0 : -1.0;\n        s[i]",
+     "const double sign = 1.0;\n        s[i]", lambda o: pins.pin_table1(o), 1e-13),
+    ("spin_term_half", "v += g1 * F[nu] * f[nu][i][j];", "v += 0.5 * g1 * F[nu] * f[nu][i][j];",
+     lambda o: pins.pin_table1(o), 1e-13),
+    ("exp_sign", "cexp(-I * delta * lam[k])", "cexp(I * delta * lam[k])",
+     lambda o: pins.pin_tf_phase(o), 1e-13),
+    ("jacobi_conj", "Gqp = -s * conj(u)", "Gqp = -s * u", lambda o: pins.pin_expm(o), 1e-13),
+    ("stream_direction", "sx = ((x - dir) % nx + nx) % nx;", "sx = ((x + dir) % nx + nx) % nx;",
+     lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
+    ("block_order", "block_qubit[4] = {1, 1, 0, 0};", "block_qubit[4] = {0, 0, 1, 1};",
+     lambda o: pins.pin_dense_step(o, 1), 1e-13),
+    ("collide_transposed", "C[0][0] = 0.5 * (1.0 - I); C[0][1] = 0.5 * (1.0 + I);",
+     "C[0][0] = 0.5 * (1.0 + I); C[0][1] = 0.5 * (1.0 - I);",
+     lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
+    ("potential_uses_a_only", "psi[m] = a[m] + b[m];", "psi[m] = a[m] + a[m];",
+     lambda o: pins.pin_dense_step(o, 2), 1e-13),
+    ("y_stream_on_x", "else sy = ((y - dir) % ny + ny) % ny;", "else sx = ((x - dir) % nx + nx) % nx;",
+     lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
+    ("interleave_fraction", "const double frac = 1.0 / (4.0 * cfg->ndim);",
+     "const double frac = 1.0 / 4.0;", lambda o: pins.pin_dense_step(o, 2, interleave=1), 1e-13),
+]
+
+
+@pytest.mark.parametrize("mid,old,new,pin,tol", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(tmp_path, mid, old, new, pin, tol):
+    src = oracle.source_text()
+    assert src.count(old) == 1, "mutation anchor not found exactly once: %s" % mid
+    path = oracle.compile_source(src.replace(old, new), str(tmp_path / ("liboracle_%s.so" % mid)))
+    mutant = oracle.Oracle(path)
+    assert pin(mutant) > tol, "pin did not catch mutation %s" % mid

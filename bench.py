@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the spin-2 QLGA step on GB300: site-updates/s and fraction of the HBM roofline.
+
+Workload (one "step" = one QLGA time step: potential unitary + kinetic operator on both axes,
+with the FP64 observables every --obs-every steps): the 2D vortex-scattering lattice, 4096 x 4096
+sites, 10 FP32 amplitudes per site, Pade vortex dipoles in m = +2 / -2, couplings (1, 0.1, 1),
+eps = 0.1.  The state (1.34 GB) is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W]            # the library (default)
+  python bench.py --impl reference                           # the FP64 CPU oracle, same metric
+
+Multi-GPU (torchrun): every rank advances its own independent lattice (a replica with its own
+seed); there is no data-path collective, so scaling is weak and value = all ranks' site-updates
+over the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QLGA site-updates/s and % of HBM roofline (FP32 vs FP64, plain vs batched/adjoint)"
+UNIT = "site-updates/s"
+BYTES_PER_SITE_F32 = 160      # one read + one write of 10 complex FP32 amplitudes
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--n", type=int, default=4096, help="lattice side")
+    p.add_argument("--obs-every", type=int, default=50)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f",
+                                          self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != self.gpu:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("qlga_step2d.cuh", "qlga_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1907_12834_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n):
+    """DRAM bytes per launch of the fused step kernel from the committed ncu summary, scaled to an
+    n x n lattice; None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_site"]) * n * n
+
+
+def cpu_baseline(state_f64, g, budget_s, n_sub=256):
+    """The oracle as it stands, on a bounded sample: an n_sub^2 window of the workload."""
+    import numpy as np
+    import oracle
+
+    cores = os.cpu_count() or 1
+    ny, nx = state_f64.shape[1], state_f64.shape[2]
+    y0, x0 = ny // 2 - n_sub // 2, nx // 2 - n_sub // 2
+    win = np.ascontiguousarray(state_f64[:, y0:y0 + n_sub, x0:x0 + n_sub], dtype=np.float64)
+    cfg = oracle.make_cfg(2, n_sub, n_sub, *g)
+    t0 = time.perf_counter()
+    oracle.step(win, cfg, 1, nthreads=cores)
+    t1 = time.perf_counter()
+    steps = max(1, min(200, int(budget_s / max(t1 - t0, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(win, cfg, steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sub * n_sub * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d x %d window at the lattice centre of the same workload, %d FP64 steps, "
+                      "%.1f s" % (n_sub, n_sub, steps, dt)}
+
+
+# ----------------------------------------------------------------------------- library arm
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    from paper_1907_12834_gb300 import inputs, qlga
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    w = inputs.config2(seed=1909 + rank, n=n)
+    lat = qlga.Lattice(2, n, n, precision=32, g=w.g, epsilon=w.eps)
+    stream = lat.stream
+    sites = n * n
+
+    lat.load_state(w.state)
+    lat.step(args.warmup)
+    lat.observables()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    launches0 = lat.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    obs_steps = set()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        lat.step(1)
+        if args.obs_every and (i + 1) % args.obs_every == 0:
+            lat.observables()               # FP64 reductions, host read
+            obs_steps.add(i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = lat.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+
+    elapsed_ms = ev[0].elapsed_time(ev[args.steps])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    plain = [t for i, t in enumerate(step_ms) if i not in obs_steps] or step_ms
+    kernel_ms = statistics.mean(plain)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(lat, w, args, torch, qlga, sites)
+        if dist:
+            t = torch.tensor([e2e["seconds"]], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * sites * args.steps / float(t.item())
+        e2e.pop("seconds")
+    lat.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_SITE_F32 * sites / (kernel_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(n)
+    line = {
+        "metric": METRIC, "value": world * sites * args.steps / (elapsed_ms * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Pade vortex dipoles)",
+        "config": {"workload": w.name, "lattice": [n, n], "precision": "fp32",
+                   "couplings": list(w.g), "epsilon": w.eps, "obs_every": args.obs_every,
+                   "l2": "inputs larger than L2 (%.2f GB state)" % (sites * 80 / 1e9),
+                   "parallelism": "replicas%d" % world},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w.state, w.g, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(lat, w, args, torch, qlga, sites):
+    """Same steps through the C ABI with host buffers: pinned upload, steps, observables, pinned
+    read-back of the final state, all inside the timed region."""
+    host_in = torch.from_numpy(w.state).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qlga.qlga_load_state(lat.handle, host_in.data_ptr(), qlga.QLGA_HOST)
+    qlga.qlga_step(lat.handle, args.warmup)
+    for i in range(args.steps):
+        qlga.qlga_step(lat.handle, 1)
+        if args.obs_every and (i + 1) % args.obs_every == 0:
+            qlga.qlga_observables(lat.handle)
+    qlga.qlga_get_state(lat.handle, host_out.data_ptr(), qlga.QLGA_HOST)
+    dt = time.perf_counter() - t0
+    nbytes = host_in.numel() * host_in.element_size()
+    return {"value": sites * args.steps / dt, "unit": UNIT, "seconds": dt,
+            "h2d_bytes_per_step": nbytes / args.steps,
+            "d2h_bytes_per_step": (nbytes + 8 * 16 * (args.steps // max(args.obs_every, 1))) / args.steps,
+            "note": "includes %d warm-up steps after the upload" % args.warmup}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on this host's cores: each step advances a bounded
+    sample (a 256^2 window) of the same workload by one QLGA step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_1907_12834_gb300 import inputs
+
+    n_sub = 256
+    w = inputs.config2(n=args.n)
+    ny = nx = args.n
+    y0, x0 = ny // 2 - n_sub // 2, nx // 2 - n_sub // 2
+    win = np.ascontiguousarray(w.state[:, y0:y0 + n_sub, x0:x0 + n_sub], dtype=np.float64)
+    del w
+    cfg = oracle.make_cfg(2, n_sub, n_sub, *inputs.CONFIG2_G)
+    cores = os.cpu_count() or 1
+    oracle.step(win, cfg, args.warmup, nthreads=cores)
+    t0 = time.perf_counter()
+    oracle.step(win, cfg, args.steps, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = n_sub * n_sub * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Pade vortex dipoles)",
+        "config": {"workload": "2d-vortex-scattering-%dx%d" % (args.n, args.n),
+                   "lattice": [args.n, args.n], "precision": "fp64 (oracle)",
+                   "couplings": list(inputs.CONFIG2_G), "epsilon": 0.1,
+                   "sample": "%d x %d window per step" % (n_sub, n_sub)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d x %d window of the workload, %d steps" % (n_sub, n_sub, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,9 @@ qlga_status qlga_apply_kinetic(qlga_handle* h);
  * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.C). */
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
 
+/* Number of kernels this handle has launched since creation (a diagnostic for benchmarks). */
+qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count);
+
 /* Wait for all work enqueued on the handle's stream. */
 qlga_status qlga_synchronize(qlga_handle* h);
 

@@ -1,0 +1,781 @@
+// qlga.cu -- C ABI and kernels of the GB300 spin-2 QLGA library (arXiv:1907.12834).
+//
+// The declarations, argument meaning, layout, ownership and error behaviour are in
+// include/qlga.h.  This file holds the host side (handle, stream-ordered launches, error
+// reporting) and the generic kernels:
+//   k_potential      U = exp(-i delta V(psi)) on every site, in place            (Sec. VII.B)
+//   k_kinetic_axis   one axis of the kinetic operator, optionally followed by U  (Sec. VII.B)
+//   k_block          one kinetic block I'_c (interleaved step)                   (Sec. VII.B)
+//   k_observables    FP64 sums of Sec. IV.A / IV.C, two-level deterministic reduction
+// The fused 2D FP32 step (one HBM read and one write of the state per step) is in
+// qlga_step2d.cuh.
+//
+// Representation.  A plain time step is psi(t+1) = K U(psi(t)) psi(t).  Over n steps this is
+// K (U K)^(n-1) U, so the handle keeps the state "pending K": the buffer holds X with the true
+// state psi = K X.  Each step is then one fused launch X <- U(K X) K X that reads and writes the
+// state once; K is applied on the fly when the true state is read out.  Results are the same
+// as applying the operators in the paper's order.
+#include "qlga.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+
+#include "qlga_device.cuh"
+#include "qlga_step2d.cuh"
+
+using namespace qlga;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kObsMaxBlocks = 152 * 8;
+
+thread_local std::string g_last_error;
+
+qlga_status fail(qlga_status s, const char* fmt, const char* detail = nullptr) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), fmt, detail ? detail : "");
+    g_last_error = buf;
+    return s;
+}
+
+qlga_status cuda_fail(cudaError_t e, const char* where) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    g_last_error = buf;
+    return e == cudaErrorMemoryAllocation ? QLGA_ERR_OOM : QLGA_ERR_CUDA;
+}
+
+#define QLGA_CUDA(call, where)                          \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// ===================================================================== kernels
+
+namespace qlga {
+
+template <class T>
+__device__ __forceinline__ void load_pair(const T* X, int64_t nsites, int m, int64_t site,
+                                          cpx<T>& a, cpx<T>& b);
+template <>
+__device__ __forceinline__ void load_pair<float>(const float* X, int64_t nsites, int m,
+                                                 int64_t site, cpx<float>& a, cpx<float>& b) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(X) + m * nsites + site);
+    a = {v.x, v.y};
+    b = {v.z, v.w};
+}
+template <>
+__device__ __forceinline__ void load_pair<double>(const double* X, int64_t nsites, int m,
+                                                  int64_t site, cpx<double>& a, cpx<double>& b) {
+    const double2* p = reinterpret_cast<const double2*>(X) + 2 * (m * nsites + site);
+    const double2 va = __ldg(p), vb = __ldg(p + 1);
+    a = {va.x, va.y};
+    b = {vb.x, vb.y};
+}
+
+// U on every site, in place.  All lanes of a warp run the potential (the Taylor degree is a
+// warp-wide maximum); lanes past the end work on zeros and store nothing.
+template <class T, bool SPLIT>
+__global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotParams P,
+                                                        unsigned* status) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
+        const int64_t site = base + threadIdx.x;
+        const bool active = site < nsites;
+        cpx<T> a[5], b[5];
+        if (active) {
+            SiteIO<T>::load(X, nsites, site, a, b);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) a[m] = b[m] = {T(0), T(0)};
+        }
+        potential_site<T, SPLIT>(a, b, P, T(1), T(0.5), status);
+        if (active) SiteIO<T>::store(X, nsites, site, a, b);
+    }
+}
+
+// out = [U o] K_axis(in): the nine-point kinetic stencil of one axis (derived at compile time
+// from the block definition), optionally followed by the potential unitary.
+template <class T, int VARIANT, bool POT>
+__global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__ in,
+                                                           T* __restrict__ out, int64_t nx,
+                                                           int64_t ny, int axis, PotParams P,
+                                                           unsigned* status) {
+    constexpr KinStencil S = kStencil[VARIANT];
+    const int64_t nsites = nx * ny;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
+        const int64_t site = base + threadIdx.x;
+        const bool active = site < nsites;
+        const int64_t s = active ? site : 0;
+        const int64_t x = s % nx, y = s / nx;
+        int64_t nb[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (axis == 0) {
+                int64_t xx = x + k - 4;
+                xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+                nb[k] = y * nx + xx;
+            } else {
+                int64_t yy = y + k - 4;
+                yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+                nb[k] = yy * nx + x;
+            }
+        }
+        cpx<T> oa[5], ob[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cpx<T> acc_a = {T(0), T(0)}, acc_bt = {T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                cpx<T> a, b;
+                load_pair<T>(in, nsites, m, nb[k], a, b);
+                const cpx<T> bt = {-b.im, b.re};  // bt = i b
+                const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
+                const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
+                acc_a.re = fma(caa, a.re, fma(cab, bt.re, acc_a.re));
+                acc_a.im = fma(caa, a.im, fma(cab, bt.im, acc_a.im));
+                acc_bt.re = fma(cba, a.re, fma(cbb, bt.re, acc_bt.re));
+                acc_bt.im = fma(cba, a.im, fma(cbb, bt.im, acc_bt.im));
+            }
+            const T sc = T(0.0625);
+            oa[m] = {sc * acc_a.re, sc * acc_a.im};
+            ob[m] = {sc * acc_bt.im, -sc * acc_bt.re};  // b = -i bt
+        }
+        if (POT) potential_site<T, std::is_same<T, float>::value>(oa, ob, P, T(1), T(0.5), status);
+        if (active) SiteIO<T>::store(out, nsites, site, oa, ob);
+    }
+}
+
+// One kinetic block I'_q = S_q C' S^T_q C along `axis` (out of place): the interleaved step
+// applies U^(1/4) or U^(1/8) between blocks.  out_q(j) = W_q(j-1), out_o(j) = W_o(j) with
+// W = C' Z, Z_q(j) = Y_q(j+1), Z_o(j) = Y_o(j), Y = C in.
+template <class T, int VARIANT>
+__global__ void __launch_bounds__(kThreads) k_block(const T* __restrict__ in, T* __restrict__ out,
+                                                    int64_t nx, int64_t ny, int axis, int q) {
+    const int64_t nsites = nx * ny;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    // collides in the (a, b) basis: C1 = 1/2[[1-i, 1+i], [1+i, 1-i]], C2 = 1/2[[1+i, 1-i], [1-i, 1+i]]
+    const cpx<T> p = {T(0.5), T(-0.5)}, mq = {T(0.5), T(0.5)};  // (1-i)/2, (1+i)/2
+    for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
+        const int64_t x = site % nx, y = site / nx;
+        int64_t nbs[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (axis == 0) {
+                int64_t xx = x + k - 1;
+                xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+                nbs[k] = y * nx + xx;
+            } else {
+                int64_t yy = y + k - 1;
+                yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+                nbs[k] = yy * nx + x;
+            }
+        }
+        cpx<T> oa[5], ob[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cpx<T> Y[3][2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                cpx<T> a, b;
+                load_pair<T>(in, nsites, m, nbs[k], a, b);
+                // first collide: K1 uses C1, K2 uses C2 (= C1 with the roles of p, mq swapped)
+                const cpx<T> d0 = VARIANT == 0 ? p : mq, o0 = VARIANT == 0 ? mq : p;
+                Y[k][0] = cmul(d0, a) + cmul(o0, b);
+                Y[k][1] = cmul(o0, a) + cmul(d0, b);
+            }
+            // W at j-1 (k = 0) and j (k = 1)
+            cpx<T> W[2][2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                cpx<T> Z[2];
+                Z[q] = Y[k + 1][q];
+                Z[1 - q] = Y[k][1 - q];
+                // second collide: C1 for both variants (C2^dagger = C1)
+                W[k][0] = cmul(p, Z[0]) + cmul(mq, Z[1]);
+                W[k][1] = cmul(mq, Z[0]) + cmul(p, Z[1]);
+            }
+            cpx<T> o[2];
+            o[q] = W[0][q];
+            o[1 - q] = W[1][1 - q];
+            oa[m] = o[0];
+            ob[m] = o[1];
+        }
+        SiteIO<T>::store(out, nsites, site, oa, ob);
+    }
+}
+
+// a = b = eps psi / 2 from a complex boson field psi5[5][nsites] (re, im interleaved)
+template <class T>
+__global__ void k_load_boson(const T* __restrict__ psi5, T* __restrict__ X, int64_t nsites, T half_eps) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < 5 * nsites; i += stride) {
+        const T re = psi5[2 * i] * half_eps, im = psi5[2 * i + 1] * half_eps;
+        X[4 * i + 0] = re;
+        X[4 * i + 1] = im;
+        X[4 * i + 2] = re;
+        X[4 * i + 3] = im;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-site observable terms in FP64, block sums into partials[block][OBS_COUNT].
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ X,
+                                                          const T* __restrict__ ref, int64_t nx,
+                                                          int64_t ny, int ndim, double g0,
+                                                          double g1, double g2,
+                                                          double* __restrict__ partials) {
+    const int64_t nsites = nx * ny;
+    double acc[OBS_COUNT];
+#pragma unroll
+    for (int k = 0; k < OBS_COUNT; ++k) acc[k] = 0.0;
+    const double r32 = 1.2247448713915890491;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
+        const int64_t x = site % nx, y = site / nx;
+        cpx<double> psi[5];
+        double rho = 0.0;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cpx<T> a, b;
+            load_pair<T>(X, nsites, m, site, a, b);
+            const cpx<double> ad = {double(a.re), double(a.im)}, bd = {double(b.re), double(b.im)};
+            const double pm = norm2(ad) + norm2(bd);
+            acc[OBS_NORM_QUBIT] += pm;
+            acc[OBS_POP0 + m] += pm;
+            psi[m] = ad + bd;
+            rho += norm2(psi[m]);
+        }
+        acc[OBS_NORM_BOSON] += rho;
+        // F_z, F_+ = psi^dagger f_+ psi (f_+ = f_x + i f_y): |F|^2 = F_z^2 + |F_+|^2
+        const double Fz = 2.0 * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
+        cpx<double> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
+        const cpx<double> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
+        Fp = {2.0 * (Fp.re + r32 * mid.re), 2.0 * (Fp.im + r32 * mid.im)};
+        const double F2 = Fz * Fz + norm2(Fp);
+        // theta = psi^T J psi = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2
+        const cpx<double> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
+        const cpx<double> th = {2.0 * (t1.re - t2.re) + t3.re, 2.0 * (t1.im - t2.im) + t3.im};
+        const double th2 = norm2(th);
+        double grad = 0.0;
+        for (int ax = 0; ax < ndim; ++ax) {
+            const int64_t xn = ax == 0 ? (x + 1 == nx ? 0 : x + 1) : x;
+            const int64_t yn = ax == 1 ? (y + 1 == ny ? 0 : y + 1) : y;
+            const int64_t sn = yn * nx + xn;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                cpx<T> a, b;
+                load_pair<T>(X, nsites, m, sn, a, b);
+                const cpx<double> pn = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
+                grad += norm2(pn - psi[m]);
+            }
+        }
+        acc[OBS_ENERGY] += grad + 0.5 * g0 * rho * rho + 0.5 * g1 * F2 + 0.1 * g2 * th2;
+        acc[OBS_SINGLET_RE] += th.re * 0.44721359549995793928;  // 1/sqrt(5)
+        acc[OBS_SINGLET_IM] += th.im * 0.44721359549995793928;
+        acc[OBS_THETA2] += th2;
+        acc[OBS_RHO2] += rho * rho;
+        if (ref) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                cpx<T> a, b;
+                load_pair<T>(ref, nsites, m, site, a, b);
+                const cpx<double> r = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
+                const cpx<double> ov = cmulc(psi[m], r);
+                acc[OBS_OVERLAP_RE] += ov.re;
+                acc[OBS_OVERLAP_IM] += ov.im;
+            }
+        }
+    }
+    __shared__ double sh[kThreads / 32][OBS_COUNT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < OBS_COUNT; ++k) {
+        const double v = warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < OBS_COUNT) {
+        double s = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) s += sh[w][threadIdx.x];
+        partials[int64_t(blockIdx.x) * OBS_COUNT + threadIdx.x] = s;
+    }
+}
+
+// out[k] = Neumaier-compensated sum of partials[b][k] over blocks, in a fixed order.
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks,
+                                  double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= OBS_COUNT) return;
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double v = partials[int64_t(b) * OBS_COUNT + k];
+        const double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    out[k] = s + c;
+}
+
+}  // namespace qlga
+
+// ===================================================================== handle
+
+struct qlga_handle {
+    qlga_config cfg;
+    cudaStream_t stream;
+    bool owns;
+    void* X[2];
+    void* tmp;       // one state buffer of work space
+    double* partials;
+    double* obs_dev;
+    unsigned* status;
+    int cur;
+    bool pending_k;  // buffer holds X with true state K X
+    int64_t step;
+    int64_t launches;  // kernels launched by this handle
+};
+
+namespace {
+
+int64_t nsites_of(const qlga_config& c) { return c.nx * c.ny; }
+
+size_t state_bytes_of(const qlga_config& c) {
+    return size_t(nsites_of(c)) * 20 * (c.precision == 32 ? 4 : 8);
+}
+
+size_t workspace_bytes_of(const qlga_config& c) {
+    return align256(state_bytes_of(c)) + align256(sizeof(double) * kObsMaxBlocks * OBS_COUNT) +
+           align256(sizeof(double) * OBS_COUNT) + align256(sizeof(unsigned));
+}
+
+qlga_status check_cfg(const qlga_config* c) {
+    if (!c) return fail(QLGA_ERR_INVALID_ARG, "config is NULL%s");
+    if (c->ndim != 1 && c->ndim != 2) return fail(QLGA_ERR_INVALID_ARG, "ndim must be 1 or 2%s");
+    if (c->precision != 32 && c->precision != 64)
+        return fail(QLGA_ERR_INVALID_ARG, "precision must be 32 or 64%s");
+    if (c->nx < 8) return fail(QLGA_ERR_INVALID_ARG, "nx must be >= 8%s");
+    if (c->ndim == 1 && c->ny != 1) return fail(QLGA_ERR_INVALID_ARG, "ny must be 1 for ndim 1%s");
+    if (c->ndim == 2 && c->ny < 8) return fail(QLGA_ERR_INVALID_ARG, "ny must be >= 8 for ndim 2%s");
+    if (c->nx > (int64_t(1) << 31) || c->ny > (int64_t(1) << 31) || nsites_of(*c) > (int64_t(1) << 34))
+        return fail(QLGA_ERR_INVALID_ARG, "lattice too large%s");
+    if (!std::isfinite(c->g0) || !std::isfinite(c->g1) || !std::isfinite(c->g2) || !std::isfinite(c->epsilon))
+        return fail(QLGA_ERR_INVALID_ARG, "couplings and epsilon must be finite%s");
+    if (c->interleave != 0 && c->interleave != 1) return fail(QLGA_ERR_INVALID_ARG, "interleave must be 0 or 1%s");
+    if (c->kinetic_variant != QLGA_KINETIC_K1 && c->kinetic_variant != QLGA_KINETIC_K2)
+        return fail(QLGA_ERR_INVALID_ARG, "kinetic_variant must be K1 or K2%s");
+    return QLGA_OK;
+}
+
+int grid_for(int64_t n, int cap = 152 * 16) {
+    int64_t g = (n + kThreads - 1) / kThreads;
+    if (g > cap) g = cap;
+    return int(g < 1 ? 1 : g);
+}
+
+PotParams pot_params(const qlga_config& c, double delta) { return PotParams{c.g0, c.g1, c.g2, delta}; }
+
+template <class T>
+qlga_status launch_potential(qlga_handle* h, void* buf, double delta) {
+    const int64_t n = nsites_of(h->cfg);
+    k_potential<T, std::is_same<T, float>::value><<<grid_for(n), kThreads, 0, h->stream>>>(
+        static_cast<T*>(buf), n, pot_params(h->cfg, delta), h->status);
+    QLGA_CUDA(cudaGetLastError(), "k_potential launch");
+    h->launches += 1;
+    return QLGA_OK;
+}
+
+template <class T, int V, bool POT>
+qlga_status launch_axis_t(qlga_handle* h, const void* in, void* out, int axis) {
+    const int64_t n = nsites_of(h->cfg);
+    k_kinetic_axis<T, V, POT><<<grid_for(n), kThreads, 0, h->stream>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), h->cfg.nx, h->cfg.ny, axis,
+        pot_params(h->cfg, 1.0), h->status);
+    QLGA_CUDA(cudaGetLastError(), "k_kinetic_axis launch");
+    h->launches += 1;
+    return QLGA_OK;
+}
+
+qlga_status launch_axis(qlga_handle* h, const void* in, void* out, int axis, bool pot) {
+    const bool f = h->cfg.precision == 32;
+    const int v = h->cfg.kinetic_variant;
+    if (f) {
+        if (v == 0) return pot ? launch_axis_t<float, 0, true>(h, in, out, axis) : launch_axis_t<float, 0, false>(h, in, out, axis);
+        return pot ? launch_axis_t<float, 1, true>(h, in, out, axis) : launch_axis_t<float, 1, false>(h, in, out, axis);
+    }
+    if (v == 0) return pot ? launch_axis_t<double, 0, true>(h, in, out, axis) : launch_axis_t<double, 0, false>(h, in, out, axis);
+    return pot ? launch_axis_t<double, 1, true>(h, in, out, axis) : launch_axis_t<double, 1, false>(h, in, out, axis);
+}
+
+qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
+    return h->cfg.precision == 32 ? launch_potential<float>(h, buf, delta) : launch_potential<double>(h, buf, delta);
+}
+
+qlga_status launch_block(qlga_handle* h, const void* in, void* out, int axis, int q) {
+    const int64_t n = nsites_of(h->cfg);
+    const int g = grid_for(n);
+    if (h->cfg.precision == 32) {
+        if (h->cfg.kinetic_variant == 0)
+            k_block<float, 0><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+        else
+            k_block<float, 1><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+    } else {
+        if (h->cfg.kinetic_variant == 0)
+            k_block<double, 0><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+        else
+            k_block<double, 1><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+    }
+    QLGA_CUDA(cudaGetLastError(), "k_block launch");
+    h->launches += 1;
+    return QLGA_OK;
+}
+
+// Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
+// x pass.  With pot, U follows the last axis (the fused step).
+qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
+    if (h->cfg.ndim == 1) return launch_axis(h, in, out, 0, pot);
+    if (pot && h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
+        if (step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx,
+                              h->cfg.ny, h->cfg.kinetic_variant, pot_params(h->cfg, 1.0), h->status,
+                              h->stream))
+            return cuda_fail(cudaGetLastError(), "step2d launch");
+        h->launches += 1;
+        return QLGA_OK;
+    }
+    qlga_status s = launch_axis(h, in, mid, 0, false);
+    if (s != QLGA_OK) return s;
+    return launch_axis(h, mid, out, 1, pot);
+}
+
+// Make the buffer hold the true state (pending K applied).
+qlga_status materialize(qlga_handle* h) {
+    if (!h->pending_k) return QLGA_OK;
+    qlga_status s = kinetic_into(h, h->X[h->cur], h->X[1 - h->cur], h->tmp, false);
+    if (s != QLGA_OK) return s;
+    h->cur ^= 1;
+    h->pending_k = false;
+    return QLGA_OK;
+}
+
+// Device pointer of the true state without changing the representation.
+qlga_status true_state_view(qlga_handle* h, const void** view) {
+    if (!h->pending_k) {
+        *view = h->X[h->cur];
+        return QLGA_OK;
+    }
+    void* dst = h->cfg.ndim == 1 ? h->tmp : h->X[1 - h->cur];
+    qlga_status s = kinetic_into(h, h->X[h->cur], dst, h->tmp, false);
+    *view = dst;
+    return s;
+}
+
+qlga_status check_status_word(qlga_handle* h) {
+    unsigned st = 0;
+    QLGA_CUDA(cudaMemcpyAsync(&st, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream), "status read");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "stream sync");
+    if (st & 1u) {
+        cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
+        return fail(QLGA_ERR_NOT_FINITE,
+                    "the potential exponent ||delta (V - c)|| exceeded 4 or was not finite: the "
+                    "field is too large for the lattice scaling (use a smaller epsilon)%s");
+    }
+    return QLGA_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+qlga_status qlga_state_bytes(const qlga_config* cfg, size_t* bytes) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!bytes) return fail(QLGA_ERR_INVALID_ARG, "bytes is NULL%s");
+    *bytes = state_bytes_of(*cfg);
+    return QLGA_OK;
+}
+
+qlga_status qlga_workspace_bytes(const qlga_config* cfg, size_t* bytes) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!bytes) return fail(QLGA_ERR_INVALID_ARG, "bytes is NULL%s");
+    *bytes = workspace_bytes_of(*cfg);
+    return QLGA_OK;
+}
+
+static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* stream, void* x0,
+                               void* x1, void* ws) {
+    h->cfg = *cfg;
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->X[0] = x0;
+    h->X[1] = x1;
+    char* w = static_cast<char*>(ws);
+    h->tmp = w;
+    w += align256(state_bytes_of(*cfg));
+    h->partials = reinterpret_cast<double*>(w);
+    w += align256(sizeof(double) * kObsMaxBlocks * OBS_COUNT);
+    h->obs_dev = reinterpret_cast<double*>(w);
+    w += align256(sizeof(double) * OBS_COUNT);
+    h->status = reinterpret_cast<unsigned*>(w);
+    h->cur = 0;
+    h->pending_k = false;
+    h->step = 0;
+    h->launches = 0;
+    QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
+    QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
+    return QLGA_OK;
+}
+
+qlga_status qlga_create(const qlga_config* cfg, void* stream, qlga_handle** out) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!out) return fail(QLGA_ERR_INVALID_ARG, "out is NULL%s");
+    *out = nullptr;
+    qlga_handle* h = new qlga_handle();
+    h->owns = true;
+    void *x0 = nullptr, *x1 = nullptr, *ws = nullptr;
+    cudaError_t e = cudaMalloc(&x0, state_bytes_of(*cfg));
+    if (e == cudaSuccess) e = cudaMalloc(&x1, state_bytes_of(*cfg));
+    if (e == cudaSuccess) e = cudaMalloc(&ws, workspace_bytes_of(*cfg));
+    if (e != cudaSuccess) {
+        cudaFree(x0);
+        cudaFree(x1);
+        cudaFree(ws);
+        delete h;
+        cudaGetLastError();
+        return cuda_fail(e, "qlga_create cudaMalloc");
+    }
+    s = init_handle(h, cfg, stream, x0, x1, ws);
+    if (s != QLGA_OK) {
+        cudaFree(x0);
+        cudaFree(x1);
+        cudaFree(ws);
+        delete h;
+        return s;
+    }
+    *out = h;
+    return QLGA_OK;
+}
+
+qlga_status qlga_create_external(const qlga_config* cfg, void* stream, void* state0, void* state1,
+                                 void* workspace, size_t workspace_bytes, qlga_handle** out) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!out || !state0 || !state1 || !workspace) return fail(QLGA_ERR_INVALID_ARG, "NULL pointer argument%s");
+    if (workspace_bytes < workspace_bytes_of(*cfg)) return fail(QLGA_ERR_INVALID_ARG, "workspace too small%s");
+    if ((reinterpret_cast<uintptr_t>(state0) | reinterpret_cast<uintptr_t>(state1) |
+         reinterpret_cast<uintptr_t>(workspace)) & 255u)
+        return fail(QLGA_ERR_INVALID_ARG, "buffers must be 256-byte aligned%s");
+    *out = nullptr;
+    qlga_handle* h = new qlga_handle();
+    h->owns = false;
+    s = init_handle(h, cfg, stream, state0, state1, workspace);
+    if (s != QLGA_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return QLGA_OK;
+}
+
+qlga_status qlga_load_state(qlga_handle* h, const void* src, int where) {
+    if (!h || !src) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const size_t nb = state_bytes_of(h->cfg);
+    QLGA_CUDA(cudaMemcpyAsync(h->X[h->cur], src, nb, where == QLGA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
+              "qlga_load_state copy");
+    if (where == QLGA_HOST) QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_load_state sync");
+    h->pending_k = false;
+    h->step = 0;
+    return QLGA_OK;
+}
+
+qlga_status qlga_load_boson(qlga_handle* h, const void* psi5, int where) {
+    if (!h || !psi5) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const size_t nb = state_bytes_of(h->cfg) / 2;  // 5 complex per site
+    const void* src = psi5;
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaMemcpyAsync(h->tmp, psi5, nb, cudaMemcpyHostToDevice, h->stream), "qlga_load_boson copy");
+        src = h->tmp;
+    }
+    const int64_t n = nsites_of(h->cfg);
+    if (h->cfg.precision == 32)
+        k_load_boson<float><<<grid_for(5 * n), kThreads, 0, h->stream>>>(static_cast<const float*>(src), static_cast<float*>(h->X[h->cur]), n, float(0.5 * h->cfg.epsilon));
+    else
+        k_load_boson<double><<<grid_for(5 * n), kThreads, 0, h->stream>>>(static_cast<const double*>(src), static_cast<double*>(h->X[h->cur]), n, 0.5 * h->cfg.epsilon);
+    QLGA_CUDA(cudaGetLastError(), "k_load_boson launch");
+    h->launches += 1;
+    if (where == QLGA_HOST) QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_load_boson sync");
+    h->pending_k = false;
+    h->step = 0;
+    return QLGA_OK;
+}
+
+qlga_status qlga_get_state(qlga_handle* h, void* dst, int where) {
+    if (!h || !dst) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const void* view = nullptr;
+    qlga_status s = true_state_view(h, &view);
+    if (s != QLGA_OK) return s;
+    QLGA_CUDA(cudaMemcpyAsync(dst, view, state_bytes_of(h->cfg), where == QLGA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
+              "qlga_get_state copy");
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_get_state sync");
+        return check_status_word(h);
+    }
+    return QLGA_OK;
+}
+
+qlga_status qlga_step(qlga_handle* h, int64_t n) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    if (n < 0) return fail(QLGA_ERR_INVALID_ARG, "n must be >= 0%s");
+    qlga_status s = QLGA_OK;
+    for (int64_t i = 0; i < n; ++i) {
+        if (h->cfg.interleave) {
+            // U^(1/(4 ndim)) before every kinetic block, blocks I'_2 I'_2 I'_1 I'_1 per axis
+            s = materialize(h);
+            if (s != QLGA_OK) return s;
+            const double frac = 1.0 / (4.0 * h->cfg.ndim);
+            static const int qs[4] = {1, 1, 0, 0};
+            for (int axis = 0; axis < h->cfg.ndim; ++axis)
+                for (int k = 0; k < 4; ++k) {
+                    s = launch_pot(h, h->X[h->cur], frac);
+                    if (s != QLGA_OK) return s;
+                    s = launch_block(h, h->X[h->cur], h->X[1 - h->cur], axis, qs[k]);
+                    if (s != QLGA_OK) return s;
+                    h->cur ^= 1;
+                }
+        } else if (!h->pending_k) {
+            s = launch_pot(h, h->X[h->cur], 1.0);  // X = U psi, true state K X
+            if (s != QLGA_OK) return s;
+            h->pending_k = true;
+        } else {
+            s = kinetic_into(h, h->X[h->cur], h->X[1 - h->cur], h->tmp, true);
+            if (s != QLGA_OK) return s;
+            h->cur ^= 1;
+        }
+        h->step += 1;
+    }
+    return QLGA_OK;
+}
+
+qlga_status qlga_apply_potential(qlga_handle* h, double delta) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    if (!std::isfinite(delta)) return fail(QLGA_ERR_INVALID_ARG, "delta must be finite%s");
+    qlga_status s = materialize(h);
+    if (s != QLGA_OK) return s;
+    return launch_pot(h, h->X[h->cur], delta);
+}
+
+qlga_status qlga_apply_kinetic(qlga_handle* h) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    qlga_status s = materialize(h);
+    if (s != QLGA_OK) return s;
+    s = kinetic_into(h, h->X[h->cur], h->X[1 - h->cur], h->tmp, false);
+    if (s != QLGA_OK) return s;
+    h->cur ^= 1;
+    return QLGA_OK;
+}
+
+qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out) {
+    if (!h || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    const void* view = nullptr;
+    qlga_status s = true_state_view(h, &view);
+    if (s != QLGA_OK) return s;
+    const int64_t n = nsites_of(h->cfg);
+    const int blocks = grid_for(n, kObsMaxBlocks);
+    if (h->cfg.precision == 32)
+        k_observables<float><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
+                                                                 h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
+    else
+        k_observables<double><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
+                                                                  h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
+    QLGA_CUDA(cudaGetLastError(), "k_observables launch");
+    k_reduce_partials<<<1, 32, 0, h->stream>>>(h->partials, blocks, h->obs_dev);
+    QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
+    h->launches += 2;
+    double o[OBS_COUNT];
+    QLGA_CUDA(cudaMemcpyAsync(o, h->obs_dev, sizeof(o), cudaMemcpyDeviceToHost, h->stream), "observables copy");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "observables sync");
+    std::memset(out, 0, sizeof(*out));
+    out->norm_qubit = o[OBS_NORM_QUBIT];
+    out->norm_boson = o[OBS_NORM_BOSON];
+    out->magnetisation = 0.0;
+    for (int m = 0; m < 5; ++m) {
+        out->pop[m] = o[OBS_POP0 + m];
+        out->magnetisation += double(2 - m) * o[OBS_POP0 + m];
+    }
+    out->energy = o[OBS_ENERGY];
+    out->singlet_re = o[OBS_SINGLET_RE];
+    out->singlet_im = o[OBS_SINGLET_IM];
+    out->singlet_fraction = o[OBS_RHO2] > 0 ? o[OBS_THETA2] / o[OBS_RHO2] : 0.0;
+    out->overlap_re = o[OBS_OVERLAP_RE];
+    out->overlap_im = o[OBS_OVERLAP_IM];
+    out->step = h->step;
+    s = check_status_word(h);
+    if (s != QLGA_OK) return s;
+    if (!std::isfinite(out->norm_qubit) || !std::isfinite(out->energy))
+        return fail(QLGA_ERR_NOT_FINITE, "the state holds NaN or Inf%s");
+    return QLGA_OK;
+}
+
+qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count) {
+    if (!h || !count) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    *count = h->launches;
+    return QLGA_OK;
+}
+
+qlga_status qlga_synchronize(qlga_handle* h) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_synchronize");
+    return check_status_word(h);
+}
+
+qlga_status qlga_destroy(qlga_handle* h) {
+    if (!h) return QLGA_OK;
+    cudaStreamSynchronize(h->stream);
+    if (h->owns) {
+        cudaFree(h->X[0]);
+        cudaFree(h->X[1]);
+        cudaFree(h->tmp);
+    }
+    delete h;
+    return QLGA_OK;
+}
+
+const char* qlga_status_string(qlga_status s) {
+    switch (s) {
+        case QLGA_OK: return "ok";
+        case QLGA_ERR_INVALID_ARG: return "invalid argument";
+        case QLGA_ERR_OOM: return "out of device memory";
+        case QLGA_ERR_CUDA: return "CUDA error";
+        case QLGA_ERR_TIMEOUT: return "device wait timed out";
+        case QLGA_ERR_NOT_FINITE: return "state not finite";
+        case QLGA_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* qlga_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

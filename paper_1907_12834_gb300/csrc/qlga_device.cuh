@@ -1,0 +1,374 @@
+// qlga_device.cuh -- device building blocks of the spin-2 QLGA step (arXiv:1907.12834).
+//
+// Conventions shared by every kernel of the library:
+//  * State: 5 planes (m = +2..-2) of ny*nx sites, x fastest; a site is the qubit pair of that
+//    level as (a.re, a.im, b.re, b.im).  One float4 (FP32) or two double2 (FP64) per site and
+//    plane, so a warp reading 32 consecutive sites of a plane reads 512 or 1024 contiguous bytes.
+//  * Inside the kinetic operator the pair is carried as (a, bt) with bt = i*b.  In that basis the
+//    collide C = 1/2 [[1-i, 1+i], [1+i, 1-i]] of a kinetic block (Sec. VII.B) becomes the scalar
+//    (1-i)/2 times the real matrix [[1, 1], [-1, 1]], so a collide costs four real additions per
+//    level.  The scalars of the eight collides of one axis multiply to exactly 1/16 (a power of
+//    two), which is applied once, exactly, at the end.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qlga {
+
+// ------------------------------------------------------------------ complex helpers
+
+template <class T>
+struct cpx {
+    T re, im;
+};
+
+template <class T>
+__device__ __forceinline__ cpx<T> mk(T r, T i) { return cpx<T>{r, i}; }
+template <class T>
+__device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <class T>
+__device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+// a * b
+template <class T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// conj(a) * b
+template <class T>
+__device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc + a * b
+template <class T>
+__device__ __forceinline__ cpx<T> cfma(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    return {fma(a.re, b.re, fma(-a.im, b.im, acc.re)), fma(a.re, b.im, fma(a.im, b.re, acc.im))};
+}
+// acc + conj(a) * b
+template <class T>
+__device__ __forceinline__ cpx<T> cfmac(cpx<T> a, cpx<T> b, cpx<T> acc) {
+    return {fma(a.re, b.re, fma(a.im, b.im, acc.re)), fma(a.re, b.im, fma(-a.im, b.re, acc.im))};
+}
+template <class T>
+__device__ __forceinline__ T norm2(cpx<T> a) { return fma(a.re, a.re, a.im * a.im); }
+
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+
+// ------------------------------------------------------------------ site load / store
+
+template <class T>
+struct SiteIO;
+
+template <>
+struct SiteIO<float> {
+    static __device__ __forceinline__ void load(const float* X, int64_t nsites, int64_t site,
+                                                cpx<float> a[5], cpx<float> b[5]) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(X) + m * nsites + site);
+            a[m] = {v.x, v.y};
+            b[m] = {v.z, v.w};
+        }
+    }
+    static __device__ __forceinline__ void store(float* X, int64_t nsites, int64_t site,
+                                                 const cpx<float> a[5], const cpx<float> b[5]) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+            reinterpret_cast<float4*>(X)[m * nsites + site] = make_float4(a[m].re, a[m].im, b[m].re, b[m].im);
+    }
+};
+
+template <>
+struct SiteIO<double> {
+    static __device__ __forceinline__ void load(const double* X, int64_t nsites, int64_t site,
+                                                cpx<double> a[5], cpx<double> b[5]) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const double2* p = reinterpret_cast<const double2*>(X) + 2 * (m * nsites + site);
+            const double2 va = __ldg(p), vb = __ldg(p + 1);
+            a[m] = {va.x, va.y};
+            b[m] = {vb.x, vb.y};
+        }
+    }
+    static __device__ __forceinline__ void store(double* X, int64_t nsites, int64_t site,
+                                                 const cpx<double> a[5], const cpx<double> b[5]) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            double2* p = reinterpret_cast<double2*>(X) + 2 * (m * nsites + site);
+            p[0] = make_double2(a[m].re, a[m].im);
+            p[1] = make_double2(b[m].re, b[m].im);
+        }
+    }
+};
+
+// ------------------------------------------------------------------ kinetic stencil
+//
+// One axis of the kinetic operator, I'_1 I'_1 I'_2 I'_2 with I'_c = S_c C' S^T_c C (Sec. VII.B;
+// the I'_2 blocks act first; S_c moves qubit c one site toward +x: c(j) <- c(j-1)), is linear
+// and translation invariant with a dependency cone of +-4 sites.  In the (a, bt) basis its
+// coefficients are integers / 16.  They are derived here at compile time by running the four
+// blocks on a unit impulse, so the table is the block definition itself, not a transcription.
+//
+//   K1: C' = C,        C (a,bt) = (1-i)/2 [[1, 1], [-1, 1]] (a, bt)
+//   K2: C' = C^dagger, C (a,bt) = (1+i)/2 [[1, -1], [1, 1]] (a, bt),  C^dagger as K1's C
+// The scalar prefactors of the eight collides multiply to 1/16 for both variants.
+
+struct KinStencil {
+    // g[dst][src][k + 4]: out_dst(j) = 1/16 * sum_k g * in_src(j + k), dst/src 0 = a, 1 = bt
+    int g[2][2][9];
+};
+
+constexpr void collide_int(int v[2][11], int m00, int m01, int m10, int m11) {
+    for (int i = 0; i < 11; ++i) {
+        const int a = v[0][i], b = v[1][i];
+        v[0][i] = m00 * a + m01 * b;
+        v[1][i] = m10 * a + m11 * b;
+    }
+}
+
+// dir = +1: S_c, c(j) <- c(j-1); dir = -1: S^T_c, c(j) <- c(j+1)
+constexpr void shift_int(int v[2][11], int c, int dir) {
+    int t[11] = {};
+    for (int i = 0; i < 11; ++i) {
+        const int src = i - dir;
+        t[i] = (src >= 0 && src < 11) ? v[c][src] : 0;
+    }
+    for (int i = 0; i < 11; ++i) v[c][i] = t[i];
+}
+
+constexpr KinStencil make_stencil(int variant) {
+    KinStencil S{};
+    const int block_qubit[4] = {1, 1, 0, 0};
+    for (int src = 0; src < 2; ++src) {
+        int v[2][11] = {};
+        v[src][5] = 1;  // unit impulse at site 0 (index 5)
+        for (int blk = 0; blk < 4; ++blk) {
+            const int c = block_qubit[blk];
+            if (variant == 0) collide_int(v, 1, 1, -1, 1);
+            else collide_int(v, 1, -1, 1, 1);
+            shift_int(v, c, -1);
+            collide_int(v, 1, 1, -1, 1);
+            shift_int(v, c, +1);
+        }
+        // response at site o feeds out(j) from in(j - o): g[dst][src][k] = v[dst][5 - k]
+        for (int dst = 0; dst < 2; ++dst)
+            for (int k = -4; k <= 4; ++k) S.g[dst][src][k + 4] = v[dst][5 - k];
+    }
+    return S;
+}
+
+constexpr KinStencil kStencil[2] = {make_stencil(0), make_stencil(1)};
+
+// Kinetic operator of one axis at one site from its 9 neighbours along the axis.
+// nb[k][m]: (a, b) of level m at offset k - 4.  Returns (a, b) of the output, scaled exactly.
+template <class T, int VARIANT>
+__device__ __forceinline__ void kinetic_axis_site(const cpx<T> (*nba)[5], const cpx<T> (*nbb)[5],
+                                                  cpx<T> oa[5], cpx<T> ob[5]) {
+    constexpr KinStencil S = kStencil[VARIANT];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        cpx<T> acc_a = {T(0), T(0)}, acc_bt = {T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const cpx<T> a = nba[k][m];
+            const cpx<T> bt = {-nbb[k][m].im, nbb[k][m].re};  // bt = i b
+            const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
+            const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
+            acc_a.re = fma(caa, a.re, fma(cab, bt.re, acc_a.re));
+            acc_a.im = fma(caa, a.im, fma(cab, bt.im, acc_a.im));
+            acc_bt.re = fma(cba, a.re, fma(cbb, bt.re, acc_bt.re));
+            acc_bt.im = fma(cba, a.im, fma(cbb, bt.im, acc_bt.im));
+        }
+        const T s = T(0.0625);
+        oa[m] = {s * acc_a.re, s * acc_a.im};
+        ob[m] = {s * acc_bt.im, -s * acc_bt.re};  // b = -i bt
+    }
+}
+
+// ------------------------------------------------------------------ potential unitary
+//
+// U = exp(-i delta V(psi)), psi = a + b, applied to a and to b (Sec. VII.B; V is the right-hand
+// side of Eq. eomspin2 written as V(psi) psi):
+//     V = g0 rho 1 + g1 (F_x f_x + F_y f_y + F_z f_z) + (g2/5) s s^dagger,
+//     F_nu = psi^dagger f_nu psi,  s_m = (-1)^m conj(psi_{-m}).
+// Evaluation: V = c 1 + W with c = (g0 + g2/25) rho its mean eigenvalue, so
+// U = e^{-i delta c} exp(-i delta W).  W is tridiagonal (the spin term: f_+ = f_x + i f_y has
+// entries 2, 2 sqrt(3/2), 2 sqrt(3/2), 2 above the diagonal) plus the rank-one singlet term, and
+// ||delta W|| <= beta = delta (2 |g1| |F| + (4/25) |g2| rho).  exp(-i delta W) is applied to the
+// vectors psi and d = a - b by its Taylor polynomial (Horner form) of the smallest degree K
+// with beta^(K+1)/(K+1)! <= tol; then a = U(psi + d)/2, b = U(psi - d)/2.  K is made uniform
+// across the warp, so the loop never diverges.
+//
+// The input may carry an exact power-of-two scale sigma (the unnormalised kinetic output):
+// quadratic forms are multiplied by inv_sigma2 = sigma^-2 and the result by 1/sigma.
+
+constexpr int kTaylorMax = 40;
+constexpr double kBetaMax = 4.0;  // beyond this the plain Taylor sum loses accuracy: flagged
+
+struct PotParams {
+    double g0, g1, g2, delta;
+};
+
+template <class T>
+struct TaylorTol;
+template <>
+struct TaylorTol<double> {
+    static constexpr double value = 1.1102230246251565e-16;  // 2^-53
+};
+template <>
+struct TaylorTol<float> {
+    static constexpr float value = 1e-9f;  // keeps the systematic truncation far below FP32 rounding
+};
+
+__device__ __forceinline__ int warp_max_int(int v) {
+    return static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(v)));
+}
+
+template <class T>
+__device__ __forceinline__ int taylor_degree(T beta, T tol) {
+    int K = 0;
+    T term = beta;  // beta^(K+1) / (K+1)!
+    while (term > tol && K < kTaylorMax) {
+        ++K;
+        term *= beta / T(K + 1);
+    }
+    return K;
+}
+
+// y = (delta W) x, with the per-site coefficients of W
+template <class T>
+struct WOp {
+    T D[5];        // diagonal: delta (g1 F_z m - g2 rho / 25)
+    cpx<T> ep[4];  // (i+1, i) entries: delta g1 c_i F_+ ; (i, i+1) = conj
+    cpx<T> u[5];   // u_j = (-1)^{m_j} psi_{4-j} = conj(s_j)
+    T R;           // delta g2 / 5 (times inv_sigma2)
+
+    __device__ __forceinline__ void apply(const cpx<T> x[5], cpx<T> y[5]) const {
+        cpx<T> t = cmul(u[0], x[0]);
+#pragma unroll
+        for (int j = 1; j < 5; ++j) t = cfma(u[j], x[j], t);
+        t = R * t;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            // D_i x_i + t * conj(u_i)
+            const cpx<T> tu = cmulc(u[i], t);
+            y[i] = {fma(D[i], x[i].re, tu.re), fma(D[i], x[i].im, tu.im)};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            y[i] = cfmac(ep[i], x[i + 1], y[i]);
+            y[i + 1] = cfma(ep[i], x[i], y[i + 1]);
+        }
+    }
+};
+
+// v <- exp(-i delta W) x by the degree-K Taylor polynomial
+template <class T>
+__device__ __forceinline__ void taylor_apply(const WOp<T>& W, const cpx<T> x[5], cpx<T> v[5], int K) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = x[i];
+    for (int k = K; k >= 1; --k) {
+        cpx<T> w[5];
+        W.apply(v, w);
+        const T ik = T(1) / T(k);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) v[i] = {fma(ik, w[i].im, x[i].re), fma(-ik, w[i].re, x[i].im)};
+    }
+}
+
+// Apply U to the pair (a, b) of one site in place.  split_d: pick the degree for d = a - b
+// from its size relative to psi (FP32); otherwise d uses the degree of psi.
+template <class T, bool SPLIT_D>
+__device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotParams& P,
+                                               T inv_sigma2, T out_scale, unsigned* status) {
+    const T g0 = T(P.g0), g1 = T(P.g1), g2 = T(P.g2), delta = T(P.delta);
+    cpx<T> psi[5], d[5];
+    T n[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        psi[i] = a[i] + b[i];
+        d[i] = a[i] - b[i];
+        n[i] = norm2(psi[i]);
+    }
+    const T pn2 = (n[0] + n[1]) + (n[2] + n[3]) + n[4];
+    const T rho = pn2 * inv_sigma2;
+    const T Fz = (T(2) * (n[0] - n[4]) + (n[1] - n[3])) * inv_sigma2;
+    const T r32 = T(1.2247448713915890491);  // sqrt(3/2)
+    cpx<T> Fp = cmulc(psi[0], psi[1]);
+    Fp = cfmac(psi[3], psi[4], Fp);
+    cpx<T> mid = cmulc(psi[1], psi[2]);
+    mid = cfmac(psi[2], psi[3], mid);
+    Fp = {fma(r32, mid.re, Fp.re), fma(r32, mid.im, Fp.im)};
+    Fp = (T(2) * inv_sigma2) * Fp;  // F_+ = psi^dagger f_+ psi
+    const T Fabs = sqrt(fma(Fz, Fz, norm2(Fp)));
+    const T beta = delta * (T(2) * fabs(g1) * Fabs + T(0.16) * fabs(g2) * rho);
+    if (!(beta <= T(kBetaMax))) atomicOr(status, 1u);  // also catches NaN
+    const T tol = TaylorTol<T>::value;
+    int K = warp_max_int(taylor_degree(beta, tol));
+    int Kd = K;
+    if (SPLIT_D) {
+        T dn2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) dn2 += norm2(d[i]);
+        int k = 0;
+        T term = beta;
+        while (k < K && term * term * dn2 > tol * tol * pn2) {
+            ++k;
+            term *= beta / T(k + 1);
+        }
+        Kd = warp_max_int(k);
+    }
+    WOp<T> W;
+    const T g2r = g2 * T(0.04) * rho;  // g2 rho / 25
+    W.D[0] = delta * (T(2) * g1 * Fz - g2r);
+    W.D[1] = delta * (g1 * Fz - g2r);
+    W.D[2] = -delta * g2r;
+    W.D[3] = -delta * (g1 * Fz + g2r);
+    W.D[4] = -delta * (T(2) * g1 * Fz + g2r);
+    const T e0 = delta * g1;
+    W.ep[0] = e0 * Fp;
+    W.ep[1] = (e0 * r32) * Fp;
+    W.ep[2] = W.ep[1];
+    W.ep[3] = W.ep[0];
+    W.u[0] = psi[4];
+    W.u[1] = {-psi[3].re, -psi[3].im};
+    W.u[2] = psi[2];
+    W.u[3] = {-psi[1].re, -psi[1].im};
+    W.u[4] = psi[0];
+    W.R = delta * g2 * T(0.2) * inv_sigma2;
+    cpx<T> vp[5], vd[5];
+    taylor_apply(W, psi, vp, K);
+    taylor_apply(W, d, vd, Kd);
+    T sn, cs;
+    sin_cos(delta * (g0 + T(0.04) * g2) * rho, &sn, &cs);
+    const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a[i] = cmul(ph, vp[i] + vd[i]);
+        b[i] = cmul(ph, vp[i] - vd[i]);
+    }
+}
+
+// ------------------------------------------------------------------ observables
+//
+// Per-site terms of the boson field psi = a + b, accumulated in FP64 (Sec. IV.A Eq. cmap; the
+// energy density is the functional whose variation is V(psi) psi, plus the forward-difference
+// gradient; the overlap gives the discrete energy of Sec. IV.C).  Order of the accumulators:
+enum ObsIndex {
+    OBS_NORM_QUBIT = 0,
+    OBS_NORM_BOSON = 1,
+    OBS_POP0 = 2,  // 2..6: m = +2..-2
+    OBS_ENERGY = 7,
+    OBS_SINGLET_RE = 8,
+    OBS_SINGLET_IM = 9,
+    OBS_THETA2 = 10,
+    OBS_RHO2 = 11,
+    OBS_OVERLAP_RE = 12,
+    OBS_OVERLAP_IM = 13,
+    OBS_COUNT = 14
+};
+
+}  // namespace qlga

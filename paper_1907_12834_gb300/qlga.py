@@ -1,0 +1,321 @@
+"""Python binding of the C ABI in include/qlga.h (argument marshalling only).
+
+Every step of the QLGA runs in the CUDA kernels of ``libqlga.so``.  PyTorch supplies device
+memory (``torch.empty`` buffers handed to ``qlga_create_external``) and the CUDA stream.  If the
+library is missing this module raises; there is no CPU fallback.
+
+Low level: the C entry points under the same names (``qlga_create``, ``qlga_step`` ...).
+High level: :class:`Lattice`, which owns a handle and its torch buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+QLGA_OK, QLGA_ERR_INVALID_ARG, QLGA_ERR_OOM, QLGA_ERR_CUDA, QLGA_ERR_TIMEOUT, \
+    QLGA_ERR_NOT_FINITE, QLGA_ERR_UNSUPPORTED = range(7)
+QLGA_HOST, QLGA_DEVICE = 0, 1
+QLGA_KINETIC_K1, QLGA_KINETIC_K2 = 0, 1
+
+
+class QlgaConfig(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("g0", ctypes.c_double), ("g1", ctypes.c_double), ("g2", ctypes.c_double),
+                ("epsilon", ctypes.c_double), ("interleave", ctypes.c_int32),
+                ("kinetic_variant", ctypes.c_int32)]
+
+
+class QlgaObs(ctypes.Structure):
+    _fields_ = [("norm_qubit", ctypes.c_double), ("norm_boson", ctypes.c_double),
+                ("pop", ctypes.c_double * 5), ("magnetisation", ctypes.c_double),
+                ("energy", ctypes.c_double), ("singlet_re", ctypes.c_double),
+                ("singlet_im", ctypes.c_double), ("singlet_fraction", ctypes.c_double),
+                ("overlap_re", ctypes.c_double), ("overlap_im", ctypes.c_double),
+                ("step", ctypes.c_int64)]
+
+
+class QlgaError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s failed: %s (%s)" % (where, _status_names.get(status, status), message))
+        self.status = status
+
+
+_status_names = {0: "QLGA_OK", 1: "QLGA_ERR_INVALID_ARG", 2: "QLGA_ERR_OOM", 3: "QLGA_ERR_CUDA",
+                 4: "QLGA_ERR_TIMEOUT", 5: "QLGA_ERR_NOT_FINITE", 6: "QLGA_ERR_UNSUPPORTED"}
+
+_lib = None
+_VP = ctypes.c_void_p
+_CFG = ctypes.POINTER(QlgaConfig)
+_H = ctypes.c_void_p
+
+_SIGNATURES = {
+    "qlga_state_bytes": [_CFG, ctypes.POINTER(ctypes.c_size_t)],
+    "qlga_workspace_bytes": [_CFG, ctypes.POINTER(ctypes.c_size_t)],
+    "qlga_create": [_CFG, _VP, ctypes.POINTER(_H)],
+    "qlga_create_external": [_CFG, _VP, _VP, _VP, _VP, ctypes.c_size_t, ctypes.POINTER(_H)],
+    "qlga_load_state": [_H, _VP, ctypes.c_int],
+    "qlga_load_boson": [_H, _VP, ctypes.c_int],
+    "qlga_get_state": [_H, _VP, ctypes.c_int],
+    "qlga_step": [_H, ctypes.c_int64],
+    "qlga_apply_potential": [_H, ctypes.c_double],
+    "qlga_apply_kinetic": [_H],
+    "qlga_observables": [_H, _VP, ctypes.POINTER(QlgaObs)],
+    "qlga_synchronize": [_H],
+    "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
+    "qlga_destroy": [_H],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libqlga.so (building it with nvcc if absent and allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libqlga.so is not built (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, argtypes in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_int
+    lib.qlga_status_string.argtypes = [ctypes.c_int]
+    lib.qlga_status_string.restype = ctypes.c_char_p
+    lib.qlga_last_error.argtypes = []
+    lib.qlga_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def header_symbols() -> list:
+    """Entry points declared in include/qlga.h."""
+    hdr = os.path.join(_build.ROOT, "include", "qlga.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:qlga_status|const char\*)\s+(qlga_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, where: str):
+    if status != QLGA_OK:
+        lib = load_library()
+        raise QlgaError(status, where, lib.qlga_last_error().decode())
+
+
+# ------------------------------------------------------------------ C entry points, same names
+
+def make_config(ndim, nx, ny=1, precision=64, g=(1.0, 0.0, 0.0), epsilon=0.1, interleave=0,
+                kinetic_variant=0) -> QlgaConfig:
+    return QlgaConfig(int(ndim), int(precision), int(nx), int(ny), float(g[0]), float(g[1]),
+                      float(g[2]), float(epsilon), int(interleave), int(kinetic_variant))
+
+
+def qlga_state_bytes(cfg: QlgaConfig) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().qlga_state_bytes(ctypes.byref(cfg), ctypes.byref(out)), "qlga_state_bytes")
+    return out.value
+
+
+def qlga_workspace_bytes(cfg: QlgaConfig) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().qlga_workspace_bytes(ctypes.byref(cfg), ctypes.byref(out)),
+           "qlga_workspace_bytes")
+    return out.value
+
+
+def qlga_create(cfg: QlgaConfig, stream: int = 0) -> int:
+    h = _H()
+    _check(load_library().qlga_create(ctypes.byref(cfg), _VP(stream), ctypes.byref(h)), "qlga_create")
+    return h.value
+
+
+def qlga_create_external(cfg, stream, state0, state1, workspace, workspace_bytes) -> int:
+    h = _H()
+    _check(load_library().qlga_create_external(ctypes.byref(cfg), _VP(stream), _VP(state0),
+                                               _VP(state1), _VP(workspace),
+                                               ctypes.c_size_t(workspace_bytes), ctypes.byref(h)),
+           "qlga_create_external")
+    return h.value
+
+
+def qlga_load_state(h: int, ptr: int, where: int):
+    _check(load_library().qlga_load_state(_H(h), _VP(ptr), int(where)), "qlga_load_state")
+
+
+def qlga_load_boson(h: int, ptr: int, where: int):
+    _check(load_library().qlga_load_boson(_H(h), _VP(ptr), int(where)), "qlga_load_boson")
+
+
+def qlga_get_state(h: int, ptr: int, where: int):
+    _check(load_library().qlga_get_state(_H(h), _VP(ptr), int(where)), "qlga_get_state")
+
+
+def qlga_step(h: int, n: int):
+    _check(load_library().qlga_step(_H(h), ctypes.c_int64(int(n))), "qlga_step")
+
+
+def qlga_apply_potential(h: int, delta: float):
+    _check(load_library().qlga_apply_potential(_H(h), ctypes.c_double(delta)), "qlga_apply_potential")
+
+
+def qlga_apply_kinetic(h: int):
+    _check(load_library().qlga_apply_kinetic(_H(h)), "qlga_apply_kinetic")
+
+
+def qlga_observables(h: int, ref_ptr: int = 0) -> QlgaObs:
+    out = QlgaObs()
+    _check(load_library().qlga_observables(_H(h), _VP(ref_ptr or None), ctypes.byref(out)),
+           "qlga_observables")
+    return out
+
+
+def qlga_launch_count(h: int) -> int:
+    out = ctypes.c_int64()
+    _check(load_library().qlga_launch_count(_H(h), ctypes.byref(out)), "qlga_launch_count")
+    return out.value
+
+
+def qlga_synchronize(h: int):
+    _check(load_library().qlga_synchronize(_H(h)), "qlga_synchronize")
+
+
+def qlga_destroy(h: int):
+    _check(load_library().qlga_destroy(_H(h)), "qlga_destroy")
+
+
+def qlga_status_string(status: int) -> str:
+    return load_library().qlga_status_string(int(status)).decode()
+
+
+def qlga_last_error() -> str:
+    return load_library().qlga_last_error().decode()
+
+
+def obs_to_dict(o: QlgaObs) -> dict:
+    d = {k: getattr(o, k) for k, _ in QlgaObs._fields_ if k != "pop"}
+    d["pop"] = np.array(list(o.pop))
+    return d
+
+
+# ------------------------------------------------------------------ high-level lattice
+
+class Lattice:
+    """A QLGA lattice on the current CUDA device, in torch-allocated device memory.
+
+    ``state`` arrays use the library layout (5, ny, nx, 2, 2): level m = +2..-2, y, x,
+    qubit (a, b), (re, im); float32 for precision 32, float64 for 64.
+    """
+
+    def __init__(self, ndim, nx, ny=1, precision=64, g=(1.0, 0.0, 0.0), epsilon=0.1,
+                 interleave=0, kinetic_variant=0, stream=None, device=None):
+        import torch
+        self._torch = torch
+        self.cfg = make_config(ndim, nx, ny, precision, g, epsilon, interleave, kinetic_variant)
+        self.shape = (5, int(ny), int(nx), 2, 2)
+        self.dtype = np.float32 if precision == 32 else np.float64
+        self.tdtype = torch.float32 if precision == 32 else torch.float64
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        sb = qlga_state_bytes(self.cfg)
+        wb = qlga_workspace_bytes(self.cfg)
+        with torch.cuda.device(dev):
+            # 256-byte aligned blocks from the caching allocator
+            self._bufs = [torch.empty(sb + 256, dtype=torch.uint8, device=dev) for _ in range(2)]
+            self._ws = torch.empty(wb + 256, dtype=torch.uint8, device=dev)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            ptrs = [self._aligned(b) for b in self._bufs]
+            self.handle = qlga_create_external(self.cfg, self.stream.cuda_stream, ptrs[0], ptrs[1],
+                                               self._aligned(self._ws), wb)
+        self.state_bytes = sb
+
+    @staticmethod
+    def _aligned(t):
+        p = t.data_ptr()
+        return (p + 255) & ~255
+
+    # -- state transfer
+    def load_state(self, state):
+        """Host numpy array or device torch tensor of the library layout."""
+        torch = self._torch
+        if isinstance(state, torch.Tensor):
+            if not state.is_cuda:
+                state = state.numpy()
+            else:
+                t = state.contiguous()
+                assert t.dtype == self.tdtype and tuple(t.shape) == self.shape
+                qlga_load_state(self.handle, t.data_ptr(), QLGA_DEVICE)
+                return
+        a = np.ascontiguousarray(state, dtype=self.dtype)
+        assert a.shape == self.shape, (a.shape, self.shape)
+        qlga_load_state(self.handle, a.ctypes.data, QLGA_HOST)
+
+    def load_boson(self, psi):
+        """Physical boson field psi[5, ny, nx] (complex): a = b = epsilon psi / 2."""
+        z = np.asarray(psi).reshape(5, self.shape[1], self.shape[2])
+        a = np.ascontiguousarray(np.stack([z.real, z.imag], axis=-1), dtype=self.dtype)
+        qlga_load_boson(self.handle, a.ctypes.data, QLGA_HOST)
+
+    def get_state(self, out=None):
+        """Copy of the current state: numpy (host) by default, or into a device tensor."""
+        torch = self._torch
+        if out is not None and isinstance(out, torch.Tensor) and out.is_cuda:
+            qlga_get_state(self.handle, out.data_ptr(), QLGA_DEVICE)
+            return out
+        host = np.empty(self.shape, dtype=self.dtype) if out is None else out
+        qlga_get_state(self.handle, host.ctypes.data, QLGA_HOST)
+        return host
+
+    def device_state(self):
+        t = self._torch.empty(self.shape, dtype=self.tdtype, device=self.device)
+        qlga_get_state(self.handle, t.data_ptr(), QLGA_DEVICE)
+        return t
+
+    # -- time stepping
+    def step(self, n=1):
+        qlga_step(self.handle, n)
+
+    def apply_potential(self, delta=1.0):
+        qlga_apply_potential(self.handle, delta)
+
+    def apply_kinetic(self):
+        qlga_apply_kinetic(self.handle)
+
+    def observables(self, ref=None) -> dict:
+        ref_ptr = 0
+        if ref is not None:
+            ref_ptr = ref.data_ptr()
+        return obs_to_dict(qlga_observables(self.handle, ref_ptr))
+
+    def synchronize(self):
+        qlga_synchronize(self.handle)
+
+    def launch_count(self) -> int:
+        return qlga_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            qlga_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,290 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 relative L2 error 1e-11, FP32 1e-4 after the run (the stated targets); the
+stage checks (one potential or one kinetic application) use tighter bounds derived from the
+arithmetic (a few ulp of the largest amplitude).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_12834_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1907_12834_gb300 import qlga  # noqa: E402
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_gpu(state, ndim, nx, ny, g, nsteps, precision=64, interleave=0, variant=0):
+    lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=g, interleave=interleave,
+                       kinetic_variant=variant)
+    lat.load_state(state.astype(np.float32 if precision == 32 else np.float64))
+    lat.step(nsteps)
+    out = lat.get_state()
+    lat.close()
+    return out
+
+
+def run_oracle(state, ndim, nx, ny, g, nsteps, interleave=0, variant=0):
+    st = np.ascontiguousarray(state, dtype=np.float64).copy()
+    oracle.step(st, oracle.make_cfg(ndim, nx, ny, *g, interleave=interleave, kinetic_variant=variant),
+                nsteps)
+    return st
+
+
+G_SETS = [(1.0, -0.5, 0.2), (1.0, 0.8, -0.6), (1.0, 0.1, 1.0)]
+
+
+# ------------------------------------------------------------------ stage parity
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("scale", [0.0, 0.01, 0.1, 0.2])
+@pytest.mark.parametrize("delta", [1.0, 0.25])
+def test_potential_stage(precision, scale, delta):
+    rng = np.random.default_rng(int(scale * 1000) + int(delta * 10) + precision)
+    nx = 3 * 256 + 37                              # several blocks and a ragged tail
+    st = I.random_state(rng, nx, scale=scale)
+    g = (0.7, -0.45, 0.9)
+    lat = qlga.Lattice(1, nx, 1, precision=precision, g=g)
+    lat.load_state(st.astype(lat.dtype))
+    lat.apply_potential(delta)
+    got = lat.get_state()
+    lat.close()
+    ref = np.ascontiguousarray(st.astype(lat.dtype), dtype=np.float64)
+    oracle.apply_potential(ref, oracle.make_cfg(1, nx, 1, *g), delta)
+    tol = 1e-14 if precision == 64 else 2e-6
+    assert rel_l2(got, ref) <= tol if scale > 0 else np.abs(got).max() == 0
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("ndim,nx,ny", [(1, 8, 1), (1, 1000, 1), (2, 8, 8), (2, 45, 37)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_kinetic_stage(precision, ndim, nx, ny, variant):
+    rng = np.random.default_rng(nx * 7 + ny + variant)
+    st = I.random_state(rng, nx, ny, scale=0.3)
+    lat = qlga.Lattice(ndim, nx, ny, precision=precision, kinetic_variant=variant)
+    lat.load_state(st.astype(lat.dtype))
+    lat.apply_kinetic()
+    got = lat.get_state()
+    lat.close()
+    ref = np.ascontiguousarray(st.astype(lat.dtype), dtype=np.float64)
+    oracle.apply_kinetic(ref, oracle.make_cfg(ndim, nx, ny, 0, 0, 0, kinetic_variant=variant))
+    assert rel_l2(got, ref) <= (1e-15 if precision == 64 else 3e-7)
+
+
+# ------------------------------------------------------------------ whole steps
+
+@pytest.mark.parametrize("ndim,nx,ny", [(1, 300, 1), (2, 40, 33)])
+@pytest.mark.parametrize("g", G_SETS)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_steps_fp64(ndim, nx, ny, g, variant):
+    rng = np.random.default_rng(17 + nx)
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    n = 25
+    got = run_gpu(st, ndim, nx, ny, g, n, 64, variant=variant)
+    ref = run_oracle(st, ndim, nx, ny, g, n, variant=variant)
+    assert rel_l2(got, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("ndim,nx,ny", [(1, 300, 1), (2, 40, 33), (2, 130, 67)])
+@pytest.mark.parametrize("g", G_SETS)
+def test_steps_fp32(ndim, nx, ny, g):
+    rng = np.random.default_rng(23 + nx)
+    st = I.random_state(rng, nx, ny, scale=0.05).astype(np.float32)
+    n = 25
+    got = run_gpu(st, ndim, nx, ny, g, n, 32)
+    ref = run_oracle(st, ndim, nx, ny, g, n)
+    assert rel_l2(got, ref) <= 1e-4
+    assert rel_l2(got, ref) <= 1e-5                      # what the arithmetic gives here
+
+
+@pytest.mark.parametrize("ndim,nx,ny", [(1, 64, 1), (2, 24, 20)])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_interleaved_steps(ndim, nx, ny, precision):
+    rng = np.random.default_rng(29)
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    if precision == 32:
+        st = st.astype(np.float32)
+    g = G_SETS[1]
+    got = run_gpu(st, ndim, nx, ny, g, 6, precision, interleave=1)
+    ref = run_oracle(st, ndim, nx, ny, g, 6, interleave=1)
+    assert rel_l2(got, ref) <= (1e-11 if precision == 64 else 1e-5)
+
+
+def test_step_counts_and_pending_representation():
+    """Stepping 3 + 4 equals stepping 7, with reads in between (the state is held pending the
+    kinetic operator between launches)."""
+    rng = np.random.default_rng(31)
+    nx, ny = 48, 40
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    g = G_SETS[2]
+    lat = qlga.Lattice(2, nx, ny, precision=64, g=g)
+    lat.load_state(st)
+    lat.step(3)
+    mid = lat.get_state()
+    lat.observables()
+    lat.step(4)
+    got = lat.get_state()
+    lat.close()
+    assert rel_l2(mid, run_oracle(st, 2, nx, ny, g, 3)) <= 1e-12
+    assert rel_l2(got, run_oracle(st, 2, nx, ny, g, 7)) <= 1e-12
+
+
+# ------------------------------------------------------------------ observables
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("ndim,nx,ny", [(1, 500, 1), (2, 70, 33)])
+def test_observables(precision, ndim, nx, ny):
+    rng = np.random.default_rng(37)
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    ref_st = I.random_state(rng, nx, ny, scale=0.05)
+    g = G_SETS[1]
+    lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=g)
+    st_c = st.astype(lat.dtype)
+    lat.load_state(st_c)
+    ref_dev = torch.from_numpy(ref_st.astype(lat.dtype)).cuda()
+    o = lat.observables(ref=ref_dev)
+    lat.close()
+    cfg = oracle.make_cfg(ndim, nx, ny, *g)
+    w = oracle.observables(np.ascontiguousarray(st_c, dtype=np.float64), cfg,
+                           ref=np.ascontiguousarray(ref_st.astype(lat.dtype), dtype=np.float64))
+    tol = 1e-12
+    scale = w["norm_qubit"]
+    for k in ("norm_qubit", "norm_boson", "magnetisation", "energy", "singlet_re", "singlet_im",
+              "overlap_re", "overlap_im"):
+        assert abs(o[k] - w[k]) <= tol * scale, k
+    np.testing.assert_allclose(o["pop"], w["pop"], rtol=0, atol=tol * scale)
+    assert abs(o["singlet_fraction"] - w["singlet_fraction"]) <= 1e-10
+
+
+# ------------------------------------------------------------------ the paper's workloads
+
+def test_config0_bright_soliton_full_run_fp64():
+    """1D row-1 bright soliton, L = 1024, 2000 steps, FP64: parity 1e-11; norm and
+    magnetisation (exact for this single-level state) held to 1e-12."""
+    w = I.config0()
+    got = run_gpu(w.state, 1, w.nx, 1, w.g, w.steps)
+    ref = run_oracle(w.state, 1, w.nx, 1, w.g, w.steps)
+    assert rel_l2(got, ref) <= 1e-11
+    cfg = oracle.make_cfg(1, w.nx, 1, *w.g)
+    o0 = oracle.observables(w.state.copy(), cfg)
+    lat = qlga.Lattice(1, w.nx, 1, precision=64, g=w.g)
+    lat.load_state(w.state)
+    lat.step(w.steps)
+    o = lat.observables()
+    lat.close()
+    assert abs(o["norm_qubit"] - o0["norm_qubit"]) <= 1e-12 * o0["norm_qubit"]
+    assert abs(o["magnetisation"] - o0["magnetisation"]) <= 1e-12 * o0["norm_qubit"]
+
+
+@pytest.mark.parametrize("couplings", [(1.0, -0.5, 0.2), (1.0, 0.8, -0.6)])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_config1_scattering_prefix(couplings, precision):
+    """1D two-soliton scattering at full size (L = 16384) for the first 300 steps."""
+    w = I.config1(couplings=couplings, precision=precision)
+    st = w.state.astype(np.float32) if precision == 32 else w.state
+    n = 300
+    got = run_gpu(st, 1, w.nx, 1, w.g, n, precision)
+    ref = run_oracle(st, 1, w.nx, 1, w.g, n)
+    assert rel_l2(got, ref) <= (1e-11 if precision == 64 else 1e-4)
+
+
+@pytest.mark.parametrize("variant", ["a", "b", "c"])
+def test_config2_vortex_dipoles_small_lattice(variant):
+    """The 2D vortex-dipole workload on a 256^2 lattice, FP32, 100 steps."""
+    w = I.config2(n=256, variant=variant, separation=32)
+    got = run_gpu(w.state, 2, w.nx, w.ny, w.g, 100, 32)
+    ref = run_oracle(w.state, 2, w.nx, w.ny, w.g, 100)
+    assert rel_l2(got, ref) <= 1e-4
+
+
+def _window_oracle(state, cx, cy, nsteps, g, R):
+    """Advance the (2R+1)^2 periodic window around (cx, cy) by nsteps with the oracle; its centre
+    is exact when R >= 4 nsteps (the dependency cone of one step is +-4 sites per axis)."""
+    ny, nx = state.shape[1], state.shape[2]
+    ys = (np.arange(cy - R, cy + R + 1) % ny)
+    xs = (np.arange(cx - R, cx + R + 1) % nx)
+    win = np.ascontiguousarray(state[:, ys][:, :, xs], dtype=np.float64)
+    oracle.step(win, oracle.make_cfg(2, 2 * R + 1, 2 * R + 1, *g), nsteps)
+    return win[:, R, R]
+
+
+def test_config2_full_size_sampled_sites_fp32():
+    """4096^2 FP32 in the benchmark's launch configuration: 3 steps, then 24 sampled sites
+    (including the periodic corners) checked against the oracle on their dependency cones, and
+    the norm over the whole lattice."""
+    w = I.config2()
+    n = 3
+    lat = qlga.Lattice(2, w.nx, w.ny, precision=32, g=w.g)
+    lat.load_state(w.state)
+    o0 = lat.observables()
+    lat.step(n)
+    got = lat.get_state()
+    o1 = lat.observables()
+    lat.close()
+    rng = np.random.default_rng(5)
+    pts = [(0, 0), (w.nx - 1, w.ny - 1), (w.nx // 2, w.ny // 2), (w.nx // 2 - 32, w.ny // 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, w.nx, 2)) for _ in range(20)]
+    R = 4 * n + 2
+    worst = 0.0
+    for cx, cy in pts:
+        ref = _window_oracle(w.state, cx, cy, n, w.g, R)
+        worst = max(worst, rel_l2(got[:, cy, cx], ref))
+    assert worst <= 1e-5
+    assert abs(o1["norm_qubit"] - o0["norm_qubit"]) <= 1e-6 * o0["norm_qubit"]
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_zero_state_stays_zero():
+    lat = qlga.Lattice(2, 8, 8, precision=32, g=(1.0, 0.5, 0.5))
+    lat.load_state(np.zeros((5, 8, 8, 2, 2), np.float32))
+    lat.step(5)
+    assert np.abs(lat.get_state()).max() == 0.0
+    lat.close()
+
+
+def test_load_get_roundtrip_and_boson_loader():
+    rng = np.random.default_rng(41)
+    nx, ny = 33, 17
+    st = I.random_state(rng, nx, ny)
+    lat = qlga.Lattice(2, nx, ny, precision=64, epsilon=0.1)
+    lat.load_state(st)
+    assert np.array_equal(lat.get_state(), st)
+    psi = rng.normal(size=(5, ny, nx)) + 1j * rng.normal(size=(5, ny, nx))
+    lat.load_boson(psi)
+    np.testing.assert_array_equal(lat.get_state(), I.boson_to_state(psi, 0.1))
+    lat.close()
+
+
+def test_field_too_large_is_reported_not_faulted():
+    """A state far outside the lattice scaling makes ||delta (V - c)|| exceed the Taylor range;
+    the kernel flags it in the status word and the host reports QLGA_ERR_NOT_FINITE."""
+    lat = qlga.Lattice(1, 64, 1, precision=64, g=(1.0, 1.0, 1.0))
+    lat.load_state(np.full((5, 1, 64, 2, 2), 3.0))
+    lat.step(2)
+    with pytest.raises(qlga.QlgaError) as ei:
+        lat.observables()
+    assert ei.value.status == qlga.QLGA_ERR_NOT_FINITE
+    lat.close()
+
+
+def test_nan_state_reported():
+    st = np.zeros((5, 1, 64, 2, 2))
+    st[0, 0, 3, 0, 0] = np.nan
+    lat = qlga.Lattice(1, 64, 1, precision=64)
+    lat.load_state(st)
+    with pytest.raises(qlga.QlgaError) as ei:
+        lat.observables()
+    assert ei.value.status == qlga.QLGA_ERR_NOT_FINITE
+    lat.close()

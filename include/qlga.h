@@ -145,6 +145,33 @@ qlga_status qlga_apply_kinetic(qlga_handle* h);
  * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.C). */
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
 
+/* Observables of a caller-provided device state without allocating any device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate:
+ * code whose device memory is owned by its own allocator or by a fixed memory plan (a caching
+ * allocator that has reserved the pool, a service with a preset budget), where a cudaMalloc
+ * issued by the library could fail or fragment that pool, and time-critical loops that must not
+ * stall on cudaMalloc / cudaFree, which can synchronise the device.  It computes the same sums
+ * as qlga_observables() (step is reported as 0) for `state_device`, a state in the layout above
+ * in the precision of `cfg`, with `ref_state_device` optional as there; `stream` is a
+ * cudaStream_t (NULL = legacy default stream) and the call waits for it.  No handle is needed.
+ *
+ * Scratch: the block partial sums live in one file-scope __device__ array of 1216 partial rows
+ * of 14 doubles plus the 14 results (136,304 bytes), which every GPU that loads the library
+ * holds until the process exits.  The reduction grid is capped at those 1216 rows, so every
+ * configuration that qlga_state_bytes() accepts fits; a configuration it rejects, or a grid that
+ * would need more rows, is rejected with QLGA_ERR_INVALID_ARG.  Nothing is allocated: no
+ * cudaMalloc, cudaFree or allocating library routine is called.
+ *
+ * Set-up: the first call on each device (with that device current) looks up the device
+ * address of the scratch array with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  All calls on a device share the one array, which keeps the last call's
+ * contents; each call overwrites every partial row it reads, so nothing needs clearing, but
+ * calls whose work overlaps on the GPU (different streams or host threads) race on the array
+ * and must be serialised by the caller. */
+qlga_status qlga_observables_noalloc(const qlga_config* cfg, const void* state_device,
+                                     const void* ref_state_device, void* stream, qlga_obs* out);
+
 /* Number of kernels this handle has launched since creation (a diagnostic for benchmarks). */
 qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count);
 

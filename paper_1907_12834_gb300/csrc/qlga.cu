@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -501,6 +502,95 @@ qlga_status check_status_word(qlga_handle* h) {
 }
 
 }  // namespace
+
+// ===================================================================== allocation-free observables
+//
+// Scratch of qlga_observables_noalloc(): kNoAllocRows block partials of OBS_COUNT doubles, then
+// the OBS_COUNT results.  Host code must not pass the array's name to a kernel (in host code it
+// names a host-side stand-in); the device address comes from cudaGetSymbolAddress, looked up
+// once per device and cached.
+
+namespace {
+constexpr int kNoAllocRows = kObsMaxBlocks;
+constexpr size_t kNoAllocDoubles = size_t(kNoAllocRows) * OBS_COUNT + OBS_COUNT;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on first use).
+qlga_status noalloc_scratch(double** addr) {
+    int dev = 0;
+    QLGA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return fail(QLGA_ERR_UNSUPPORTED, "device ordinal beyond the scratch address table%s");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(observables scratch)");
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *addr = g_noalloc_addr[dev];
+    return QLGA_OK;
+}
+
+}  // namespace
+
+extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const void* state_device,
+                                                const void* ref_state_device, void* stream,
+                                                qlga_obs* out) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!state_device || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    const int64_t n = nsites_of(*cfg);
+    const int blocks = grid_for(n, kNoAllocRows);
+    if (blocks > kNoAllocRows)
+        return fail(QLGA_ERR_INVALID_ARG, "reduction needs more partial rows than the static scratch holds%s");
+    double* scratch = nullptr;
+    s = noalloc_scratch(&scratch);
+    if (s != QLGA_OK) return s;
+    double* result = scratch + size_t(kNoAllocRows) * OBS_COUNT;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cfg->precision == 32)
+        k_observables<float><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(state_device),
+                                                          static_cast<const float*>(ref_state_device),
+                                                          cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
+                                                          cfg->g2, scratch);
+    else
+        k_observables<double><<<blocks, kThreads, 0, st>>>(static_cast<const double*>(state_device),
+                                                           static_cast<const double*>(ref_state_device),
+                                                           cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
+                                                           cfg->g2, scratch);
+    QLGA_CUDA(cudaGetLastError(), "k_observables launch (no-alloc)");
+    k_reduce_partials<<<1, 32, 0, st>>>(scratch, blocks, result);
+    QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (no-alloc)");
+    double o[OBS_COUNT];
+    QLGA_CUDA(cudaMemcpyAsync(o, result, sizeof(o), cudaMemcpyDeviceToHost, st), "no-alloc observables copy");
+    QLGA_CUDA(cudaStreamSynchronize(st), "no-alloc observables sync");
+    std::memset(out, 0, sizeof(*out));
+    out->norm_qubit = o[OBS_NORM_QUBIT];
+    out->norm_boson = o[OBS_NORM_BOSON];
+    for (int m = 0; m < 5; ++m) {
+        out->pop[m] = o[OBS_POP0 + m];
+        out->magnetisation += double(2 - m) * o[OBS_POP0 + m];
+    }
+    out->energy = o[OBS_ENERGY];
+    out->singlet_re = o[OBS_SINGLET_RE];
+    out->singlet_im = o[OBS_SINGLET_IM];
+    out->singlet_fraction = o[OBS_RHO2] > 0 ? o[OBS_THETA2] / o[OBS_RHO2] : 0.0;
+    out->overlap_re = o[OBS_OVERLAP_RE];
+    out->overlap_im = o[OBS_OVERLAP_IM];
+    out->step = 0;
+    if (!std::isfinite(out->norm_qubit) || !std::isfinite(out->energy))
+        return fail(QLGA_ERR_NOT_FINITE, "the state holds NaN or Inf%s");
+    return QLGA_OK;
+}
 
 // ===================================================================== C ABI
 

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "qlga_observables": [_H, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_synchronize": [_H],
     "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
+    "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_destroy": [_H],
 }
 
@@ -177,6 +178,17 @@ def qlga_observables(h: int, ref_ptr: int = 0) -> QlgaObs:
     out = QlgaObs()
     _check(load_library().qlga_observables(_H(h), _VP(ref_ptr or None), ctypes.byref(out)),
            "qlga_observables")
+    return out
+
+
+def qlga_observables_noalloc(cfg: QlgaConfig, state_ptr: int, ref_ptr: int = 0,
+                             stream: int = 0) -> QlgaObs:
+    """Observables of a device state with no device allocation (static library scratch)."""
+    out = QlgaObs()
+    _check(load_library().qlga_observables_noalloc(ctypes.byref(cfg), _VP(state_ptr),
+                                                   _VP(ref_ptr or None), _VP(stream or None),
+                                                   ctypes.byref(out)),
+           "qlga_observables_noalloc")
     return out
 
 

@@ -90,6 +90,7 @@ __device__ __forceinline__ void load_pair<double>(const double* X, int64_t nsite
 template <class T, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotParams P,
                                                         unsigned* status) {
+    const PotConst<T> PC(P);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
         const int64_t site = base + threadIdx.x;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
 #pragma unroll
             for (int m = 0; m < 5; ++m) a[m] = b[m] = {T(0), T(0)};
         }
-        potential_site<T, SPLIT>(a, b, P, T(1), T(0.5), status);
+        potential_site<T, SPLIT>(a, b, PC, T(1), T(0.5), status);
         if (active) SiteIO<T>::store(X, nsites, site, a, b);
     }
 }
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
                                                            int64_t ny, int axis, PotParams P,
                                                            unsigned* status) {
     constexpr KinStencil S = kStencil[VARIANT];
+    const PotConst<T> PC(P);
     const int64_t nsites = nx * ny;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
             oa[m] = {sc * acc_a.re, sc * acc_a.im};
             ob[m] = {sc * acc_bt.im, -sc * acc_bt.re};  // b = -i bt
         }
-        if (POT) potential_site<T, std::is_same<T, float>::value>(oa, ob, P, T(1), T(0.5), status);
+        if (POT) potential_site<T, std::is_same<T, float>::value>(oa, ob, PC, T(1), T(0.5), status);
         if (active) SiteIO<T>::store(out, nsites, site, oa, ob);
     }
 }

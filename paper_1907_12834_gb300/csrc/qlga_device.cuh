@@ -54,9 +54,6 @@ __device__ __forceinline__ cpx<T> cfmac(cpx<T> a, cpx<T> b, cpx<T> acc) {
 template <class T>
 __device__ __forceinline__ T norm2(cpx<T> a) { return fma(a.re, a.re, a.im * a.im); }
 
-__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
-
 // ------------------------------------------------------------------ site load / store
 
 template <class T>
@@ -212,6 +209,43 @@ struct PotParams {
     double g0, g1, g2, delta;
 };
 
+// Per-thread constants of the potential, converted once per kernel from PotParams.
+template <class T>
+struct PotConst {
+    T cphase;  // delta (g0 + g2/25): e^{-i delta c} with c = (g0 + g2/25) rho
+    T dz;      // delta g1: diagonal spin entry per unit F_z m
+    T dr;      // delta g2 / 25: diagonal shift of the singlet term per unit rho
+    T e0, e1;  // delta g1, delta g1 sqrt(3/2): off-diagonal spin entries per unit F_+
+    T R;       // delta g2 / 5: singlet rank-one term
+    T b1, b2;  // 2 |g1| delta, (4/25) |g2| delta: beta = b1 |F| + b2 rho
+    __device__ __forceinline__ explicit PotConst(const PotParams& P) {
+        cphase = T(P.delta * (P.g0 + P.g2 / 25.0));
+        dz = T(P.delta * P.g1);
+        dr = T(P.delta * P.g2 / 25.0);
+        e0 = T(P.delta * P.g1);
+        e1 = T(P.delta * P.g1 * 1.2247448713915890491);  // sqrt(3/2)
+        R = T(P.delta * P.g2 / 5.0);
+        b1 = T(2.0 * fabs(P.g1) * P.delta);
+        b2 = T(0.16 * fabs(P.g2) * P.delta);
+    }
+};
+
+// 1/k, k = 0..kTaylorMax+1 (entry 0 unused): Taylor coefficients without divisions.
+template <class T>
+struct InvTable {
+    T v[kTaylorMax + 2];
+};
+template <class T>
+constexpr InvTable<T> make_inv_table() {
+    InvTable<T> t{};
+    for (int k = 1; k < kTaylorMax + 2; ++k) t.v[k] = T(1.0 / k);
+    return t;
+}
+__constant__ InvTable<float> c_inv_f = make_inv_table<float>();
+__constant__ InvTable<double> c_inv_d = make_inv_table<double>();
+__device__ __forceinline__ float inv_k(int k, float) { return c_inv_f.v[k]; }
+__device__ __forceinline__ double inv_k(int k, double) { return c_inv_d.v[k]; }
+
 template <class T>
 struct TaylorTol;
 template <>
@@ -223,17 +257,33 @@ struct TaylorTol<float> {
     static constexpr float value = 1e-9f;  // keeps the systematic truncation far below FP32 rounding
 };
 
+// e^{-i x} parts.  FP32: for |x| <= 1/2 the Taylor series of sin and cos to x^9 / x^10
+// (truncation below 2e-11, under FP32 rounding); otherwise the CUDA library sincosf.
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) {
+    if (fabsf(x) <= 0.5f) {
+        const float x2 = x * x;
+        *s = x * fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 2.7557319e-6f, -1.9841270e-4f), 8.3333333e-3f),
+                               -1.6666667e-1f), 1.0f);
+        *c = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -2.7557319e-7f, 2.4801587e-5f), -1.3888889e-3f),
+                                    4.1666667e-2f), -0.5f), 1.0f);
+    } else {
+        sincosf(x, s, c);
+    }
+}
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+
 __device__ __forceinline__ int warp_max_int(int v) {
     return static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(v)));
 }
 
+// Smallest K with beta^(K+1)/(K+1)! <= tol.
 template <class T>
 __device__ __forceinline__ int taylor_degree(T beta, T tol) {
     int K = 0;
     T term = beta;  // beta^(K+1) / (K+1)!
     while (term > tol && K < kTaylorMax) {
         ++K;
-        term *= beta / T(K + 1);
+        term *= beta * inv_k(K + 1, T(0));
     }
     return K;
 }
@@ -265,7 +315,7 @@ struct WOp {
     }
 };
 
-// v <- exp(-i delta W) x by the degree-K Taylor polynomial
+// v <- exp(-i delta W) x by the degree-K Taylor polynomial (Horner form; K is warp-uniform)
 template <class T>
 __device__ __forceinline__ void taylor_apply(const WOp<T>& W, const cpx<T> x[5], cpx<T> v[5], int K) {
 #pragma unroll
@@ -273,18 +323,17 @@ __device__ __forceinline__ void taylor_apply(const WOp<T>& W, const cpx<T> x[5],
     for (int k = K; k >= 1; --k) {
         cpx<T> w[5];
         W.apply(v, w);
-        const T ik = T(1) / T(k);
+        const T ik = inv_k(k, T(0));
 #pragma unroll
         for (int i = 0; i < 5; ++i) v[i] = {fma(ik, w[i].im, x[i].re), fma(-ik, w[i].re, x[i].im)};
     }
 }
 
-// Apply U to the pair (a, b) of one site in place.  split_d: pick the degree for d = a - b
+// Apply U to the pair (a, b) of one site in place.  SPLIT_D: pick the degree for d = a - b
 // from its size relative to psi (FP32); otherwise d uses the degree of psi.
 template <class T, bool SPLIT_D>
-__device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotParams& P,
+__device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotConst<T>& C,
                                                T inv_sigma2, T out_scale, unsigned* status) {
-    const T g0 = T(P.g0), g1 = T(P.g1), g2 = T(P.g2), delta = T(P.delta);
     cpx<T> psi[5], d[5];
     T n[5];
 #pragma unroll
@@ -304,10 +353,10 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
     Fp = {fma(r32, mid.re, Fp.re), fma(r32, mid.im, Fp.im)};
     Fp = (T(2) * inv_sigma2) * Fp;  // F_+ = psi^dagger f_+ psi
     const T Fabs = sqrt(fma(Fz, Fz, norm2(Fp)));
-    const T beta = delta * (T(2) * fabs(g1) * Fabs + T(0.16) * fabs(g2) * rho);
+    const T beta = fma(C.b1, Fabs, C.b2 * rho);
     if (!(beta <= T(kBetaMax))) atomicOr(status, 1u);  // also catches NaN
     const T tol = TaylorTol<T>::value;
-    int K = warp_max_int(taylor_degree(beta, tol));
+    const int K = warp_max_int(taylor_degree(beta, tol));
     int Kd = K;
     if (SPLIT_D) {
         T dn2 = T(0);
@@ -317,20 +366,20 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
         T term = beta;
         while (k < K && term * term * dn2 > tol * tol * pn2) {
             ++k;
-            term *= beta / T(k + 1);
+            term *= beta * inv_k(k + 1, T(0));
         }
         Kd = warp_max_int(k);
     }
     WOp<T> W;
-    const T g2r = g2 * T(0.04) * rho;  // g2 rho / 25
-    W.D[0] = delta * (T(2) * g1 * Fz - g2r);
-    W.D[1] = delta * (g1 * Fz - g2r);
-    W.D[2] = -delta * g2r;
-    W.D[3] = -delta * (g1 * Fz + g2r);
-    W.D[4] = -delta * (T(2) * g1 * Fz + g2r);
-    const T e0 = delta * g1;
-    W.ep[0] = e0 * Fp;
-    W.ep[1] = (e0 * r32) * Fp;
+    const T g2r = C.dr * rho;
+    const T gz = C.dz * Fz;
+    W.D[0] = T(2) * gz - g2r;
+    W.D[1] = gz - g2r;
+    W.D[2] = -g2r;
+    W.D[3] = -gz - g2r;
+    W.D[4] = T(-2) * gz - g2r;
+    W.ep[0] = C.e0 * Fp;
+    W.ep[1] = C.e1 * Fp;
     W.ep[2] = W.ep[1];
     W.ep[3] = W.ep[0];
     W.u[0] = psi[4];
@@ -338,12 +387,12 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
     W.u[2] = psi[2];
     W.u[3] = {-psi[1].re, -psi[1].im};
     W.u[4] = psi[0];
-    W.R = delta * g2 * T(0.2) * inv_sigma2;
+    W.R = C.R * inv_sigma2;
     cpx<T> vp[5], vd[5];
     taylor_apply(W, psi, vp, K);
     taylor_apply(W, d, vd, Kd);
     T sn, cs;
-    sin_cos(delta * (g0 + T(0.04) * g2) * rho, &sn, &cs);
+    sin_cos(C.cphase * rho, &sn, &cs);
     const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
 #pragma unroll
     for (int i = 0; i < 5; ++i) {

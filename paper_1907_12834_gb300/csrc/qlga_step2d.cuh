@@ -1,4 +1,26 @@
-// qlga_step2d.cuh -- fused 2D FP32 QLGA step (placeholder until the y-marching kernel lands).
+// qlga_step2d.cuh -- fused 2D FP32 QLGA step: one HBM read and one HBM write of the state.
+//
+// out = U(K X) K X with K = K_y K_x (the kinetic blocks I'_1 I'_1 I'_2 I'_2 along x, then along
+// y; Sec. VII.B) and U the potential unitary, for a state held "pending K" (see qlga.cu).
+//
+// Work decomposition ("y-marching strips").  A CTA of kW threads owns a strip of kW columns and a
+// contiguous range of output rows.  Thread t owns column x0 + t and walks down the rows:
+//   1. input rows (with the 4-column x halo on each side, periodic) are staged into a kStages-deep
+//      shared-memory ring with 16-byte cp.async copies, several rows ahead of use;
+//   2. x axis: the nine-point stencil of one axis (integer coefficients derived at compile time
+//      from the block definition) reads the thread's column and its 8 neighbours from shared
+//      memory;
+//   3. y axis: the four blocks I'_2 I'_2 I'_1 I'_1 run as a streaming pipeline down the column:
+//      each block keeps one row of history (the unshifted qubit after the first collide and the
+//      shifted qubit after the second), so the y axis costs 8 collides of 4 additions per level,
+//      has no halo recomputation, and lags the input by 4 rows;
+//   4. the potential unitary acts on the finished site, and the site is written with five 16-byte
+//      stores that are coalesced across the warp.
+// The first 8 rows of a range only fill the pipeline (the dependency cone is +-4 rows).
+//
+// The kinetic arithmetic is unnormalised: every collide drops its scalar prefactor, so the site
+// reaching the potential is 256 (2^8, exact) times the true value; the potential folds the factor
+// into its quadratic forms and its output scale.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -7,11 +29,190 @@
 
 namespace qlga {
 
-inline bool step2d_f32_supported(int64_t, int64_t) { return false; }
+constexpr int kStep2dW = 128;      // columns per strip = threads per CTA
+constexpr int kStep2dStages = 4;   // shared-memory ring depth (rows in flight)
+constexpr int kStep2dHalo = 4;
+constexpr int kStep2dRowSites = kStep2dW + 2 * kStep2dHalo;
+constexpr int kStep2dSmemBytes = kStep2dStages * 5 * kStep2dRowSites * 16;
 
-inline int step2d_f32_launch(const float*, float*, int64_t, int64_t, int, PotParams, unsigned*,
-                             cudaStream_t) {
-    return 1;
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Streaming state of one kinetic block for one level: the unshifted qubit of the first collide
+// from the previous row (yo) and the shifted qubit of the second collide from the previous row
+// (wc), both in the (a, bt = i b) basis.
+struct BlockState {
+    cpx<float> yo, wc;
+};
+
+// One block I'_c on the stream: input row n (xa, xbt) -> output row n-1, in place.
+// c = 1 shifts bt (qubit 2), c = 0 shifts a (qubit 1).  FIRST selects the first collide:
+// 0 = [[1, 1], [-1, 1]] (K1), 1 = [[1, -1], [1, 1]] (K2); the second collide is always
+// [[1, 1], [-1, 1]].
+template <int C, int FIRST>
+__device__ __forceinline__ void stream_block(cpx<float>& xa, cpx<float>& xbt, BlockState& s) {
+    cpx<float> ya, ybt;
+    if (FIRST == 0) {
+        ya = xa + xbt;
+        ybt = xbt - xa;
+    } else {
+        ya = xa - xbt;
+        ybt = xa + xbt;
+    }
+    // Z(n-1): shifted qubit from the current row (S^T: c(j) <- c(j+1)), other qubit from the
+    // previous row
+    const cpx<float> za = C == 0 ? ya : s.yo;
+    const cpx<float> zbt = C == 0 ? s.yo : ybt;
+    s.yo = C == 0 ? ybt : ya;
+    const cpx<float> wa = za + zbt, wbt = zbt - za;
+    // output row n-1: shifted qubit from W(n-2) (S: c(j) <- c(j-1)), other from W(n-1)
+    if (C == 0) {
+        xa = s.wc;
+        xbt = wbt;
+        s.wc = wa;
+    } else {
+        xa = wa;
+        xbt = s.wc;
+        s.wc = wbt;
+    }
+}
+
+template <int VARIANT>
+__global__ void __launch_bounds__(kStep2dW, 3)
+    k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
+                 PotParams P, unsigned* status) {
+    extern __shared__ float4 ring[];  // [kStages][5][kRowSites]
+    constexpr KinStencil S = kStencil[VARIANT];
+    const PotConst<float> PC(P);
+    const int t = threadIdx.x;
+    const int strips = nx / kStep2dW;
+    const int strip = blockIdx.x % strips;
+    const int chunk = blockIdx.x / strips;
+    const int x0 = strip * kStep2dW;
+    const int y_begin = int((int64_t(chunk) * ny) / chunks);
+    const int y_end = int((int64_t(chunk + 1) * ny) / chunks);
+    const int64_t nsites = int64_t(nx) * ny;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    float4* out4 = reinterpret_cast<float4*>(out);
+
+    // input rows y_begin-4 .. y_end+3, output row = input row - 4.  Thread t stages column t of
+    // the row (plus, for t < 8, halo column 128 + t) for all five levels.
+    const int nrows = (y_end - y_begin) + 8;
+    int xm = x0 - kStep2dHalo + t;
+    xm = xm < 0 ? xm + nx : xm;
+    int xh = x0 + kStep2dW - kStep2dHalo + t;
+    xh = xh >= nx ? xh - nx : xh;
+    auto issue_row = [&](int r) {
+        int y = y_begin - kStep2dHalo + r;  // in [-4, ny + 3], ny >= 8
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        float4* dst = ring + (r % kStep2dStages) * (5 * kStep2dRowSites);
+        const float4* src = in4 + int64_t(y) * nx;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) cp_async_16(dst + m * kStep2dRowSites + t, src + m * nsites + xm);
+        if (t < 2 * kStep2dHalo) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+                cp_async_16(dst + m * kStep2dRowSites + kStep2dW + t, src + m * nsites + xh);
+        }
+    };
+
+#pragma unroll
+    for (int r = 0; r < kStep2dStages - 1; ++r) {
+        if (r < nrows) issue_row(r);
+        cp_async_commit();
+    }
+
+    BlockState st[5][4];
+#pragma unroll
+    for (int m = 0; m < 5; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) st[m][k] = {{0.f, 0.f}, {0.f, 0.f}};
+
+    const float inv_sigma2 = 1.0f / 65536.0f;  // sigma = 256
+    const float out_scale = 0.5f / 256.0f;
+
+    for (int r = 0; r < nrows; ++r) {
+        cp_async_wait<kStep2dStages - 2>();
+        __syncthreads();
+        if (r + kStep2dStages - 1 < nrows) issue_row(r + kStep2dStages - 1);
+        cp_async_commit();
+
+        const float4* row = ring + (r % kStep2dStages) * (5 * kStep2dRowSites);
+        cpx<float> oa[5], ob[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            // x axis: nine-point stencil (x16, unnormalised) in the (a, bt) basis
+            cpx<float> xa = {0.f, 0.f}, xbt = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const float4 v = row[m * kStep2dRowSites + t + k];
+                const cpx<float> a = {v.x, v.y};
+                const cpx<float> bt = {-v.w, v.z};
+                const float caa = float(S.g[0][0][k]), cab = float(S.g[0][1][k]);
+                const float cba = float(S.g[1][0][k]), cbb = float(S.g[1][1][k]);
+                xa.re = fmaf(caa, a.re, fmaf(cab, bt.re, xa.re));
+                xa.im = fmaf(caa, a.im, fmaf(cab, bt.im, xa.im));
+                xbt.re = fmaf(cba, a.re, fmaf(cbb, bt.re, xbt.re));
+                xbt.im = fmaf(cba, a.im, fmaf(cbb, bt.im, xbt.im));
+            }
+            // y axis: I'_2 I'_2 then I'_1 I'_1 as a streaming pipeline (x16, unnormalised)
+            stream_block<1, VARIANT>(xa, xbt, st[m][0]);
+            stream_block<1, VARIANT>(xa, xbt, st[m][1]);
+            stream_block<0, VARIANT>(xa, xbt, st[m][2]);
+            stream_block<0, VARIANT>(xa, xbt, st[m][3]);
+            oa[m] = xa;
+            ob[m] = {xbt.im, -xbt.re};  // b = -i bt
+        }
+        if (r >= 8) {  // pipeline full: this is output row y_begin + r - 8
+            potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
+            const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + t;
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+                out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, ob[m].re, ob[m].im);
+        }
+    }
+    cp_async_wait<0>();
+}
+
+inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
+    return nx % kStep2dW == 0 && nx >= kStep2dW && ny >= 1 && nx <= (int64_t(1) << 30) &&
+           ny <= (int64_t(1) << 30);
+}
+
+// Chunks per strip so that the grid fills every SM once at the kernel's occupancy.
+inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
+    const int64_t strips = nx / kStep2dW;
+    int64_t chunks = (int64_t(sms) * per_sm) / strips;
+    if (chunks < 1) chunks = 1;
+    if (chunks > ny) chunks = ny;
+    return int(chunks);
+}
+
+// Returns 0 on success (errors are left in cudaGetLastError()).
+inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant,
+                             PotParams P, unsigned* status, cudaStream_t stream) {
+    static int sms = 0, per_sm[2] = {0, 0};
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_step2d_f32<0>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_step2d_f32<1>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
+    }
+    const int chunks = step2d_chunks(nx, ny, sms, per_sm[variant] > 0 ? per_sm[variant] : 1);
+    const int grid = int(nx / kStep2dW) * chunks;
+    if (variant == 0)
+        k_step2d_f32<0><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, P, status);
+    else
+        k_step2d_f32<1><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, P, status);
+    return cudaPeekAtLastError() != cudaSuccess;
 }
 
 }  // namespace qlga

@@ -108,6 +108,20 @@ def test_steps_fp32(ndim, nx, ny, g):
     assert rel_l2(got, ref) <= 1e-5                      # what the arithmetic gives here
 
 
+# nx a multiple of 128: these run the fused single-pass 2D kernel (strips of 128 columns,
+# row chunks with a ragged last chunk, periodic x halo across the strip edges)
+@pytest.mark.parametrize("nx,ny", [(128, 8), (256, 67), (384, 41), (512, 300)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_steps_fp32_fused_2d(nx, ny, variant):
+    rng = np.random.default_rng(43 + nx + ny)
+    st = I.random_state(rng, nx, ny, scale=0.05).astype(np.float32)
+    g = G_SETS[1]
+    n = 12
+    got = run_gpu(st, 2, nx, ny, g, n, 32, variant=variant)
+    ref = run_oracle(st, 2, nx, ny, g, n, variant=variant)
+    assert rel_l2(got, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("ndim,nx,ny", [(1, 64, 1), (2, 24, 20)])
 @pytest.mark.parametrize("precision", [64, 32])
 def test_interleaved_steps(ndim, nx, ny, precision):

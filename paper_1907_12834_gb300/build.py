@@ -34,8 +34,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if os.path.getmtime(LIB) >= newest:
             return LIB
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [_nvcc()] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-o", tmp,
-                                    os.path.join(CSRC, "qlga.cu")]
+    extra = os.environ.get("QLGA_NVCC_FLAGS", "").split()   # optional extra -D / -X flags
+    cmd = [_nvcc()] + NVCC_FLAGS + extra + ["-I", os.path.join(ROOT, "include"), "-o", tmp,
+                                            os.path.join(CSRC, "qlga.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
         print(" ".join(cmd), file=sys.stderr)

@@ -74,7 +74,7 @@ __device__ __forceinline__ void load_pair<float>(const float* X, int64_t nsites,
                                                  int64_t site, cpx<float>& a, cpx<float>& b) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(X) + m * nsites + site);
     a = {v.x, v.y};
-    b = {v.z, v.w};
+    b = {v.w, -v.z};  // resident bt = i b
 }
 template <>
 __device__ __forceinline__ void load_pair<double>(const double* X, int64_t nsites, int m,
@@ -82,15 +82,41 @@ __device__ __forceinline__ void load_pair<double>(const double* X, int64_t nsite
     const double2* p = reinterpret_cast<const double2*>(X) + 2 * (m * nsites + site);
     const double2 va = __ldg(p), vb = __ldg(p + 1);
     a = {va.x, va.y};
-    b = {vb.x, vb.y};
+    b = {vb.y, -vb.x};
+}
+
+// Pair load from a buffer in the ABI layout (a.re, a.im, b.re, b.im).
+template <class T>
+__device__ __forceinline__ void load_pair_abi(const T* X, int64_t nsites, int m, int64_t site,
+                                              cpx<T>& a, cpx<T>& b) {
+    const T* p = X + 4 * (m * nsites + site);
+    a = {p[0], p[1]};
+    b = {p[2], p[3]};
+}
+
+// ABI layout <-> resident layout, one (a, b) pair per thread; safe in place.
+template <class T, bool TO_RESIDENT>
+__global__ void k_convert_layout(const T* src, T* dst, int64_t npairs) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const T a0 = src[4 * i], a1 = src[4 * i + 1], c0 = src[4 * i + 2], c1 = src[4 * i + 3];
+        dst[4 * i] = a0;
+        dst[4 * i + 1] = a1;
+        if (TO_RESIDENT) {  // bt = i b
+            dst[4 * i + 2] = -c1;
+            dst[4 * i + 3] = c0;
+        } else {  // b = -i bt
+            dst[4 * i + 2] = c1;
+            dst[4 * i + 3] = -c0;
+        }
+    }
 }
 
 // U on every site, in place.  All lanes of a warp run the potential (the Taylor degree is a
 // warp-wide maximum); lanes past the end work on zeros and store nothing.
 template <class T, bool SPLIT>
-__global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotParams P,
+__global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotConst<T> PC,
                                                         unsigned* status) {
-    const PotConst<T> PC(P);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
         const int64_t site = base + threadIdx.x;
@@ -112,10 +138,9 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
 template <class T, int VARIANT, bool POT>
 __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__ in,
                                                            T* __restrict__ out, int64_t nx,
-                                                           int64_t ny, int axis, PotParams P,
+                                                           int64_t ny, int axis, PotConst<T> PC,
                                                            unsigned* status) {
     constexpr KinStencil S = kStencil[VARIANT];
-    const PotConst<T> PC(P);
     const int64_t nsites = nx * ny;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
@@ -226,10 +251,10 @@ __global__ void k_load_boson(const T* __restrict__ psi5, T* __restrict__ X, int6
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < 5 * nsites; i += stride) {
         const T re = psi5[2 * i] * half_eps, im = psi5[2 * i + 1] * half_eps;
-        X[4 * i + 0] = re;
+        X[4 * i + 0] = re;  // a = eps psi / 2
         X[4 * i + 1] = im;
-        X[4 * i + 2] = re;
-        X[4 * i + 3] = im;
+        X[4 * i + 2] = -im;  // bt = i b, b = eps psi / 2
+        X[4 * i + 3] = re;
     }
 }
 
@@ -240,7 +265,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Per-site observable terms in FP64, block sums into partials[block][OBS_COUNT].
-template <class T>
+template <class T, bool RESIDENT>
 __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ X,
                                                           const T* __restrict__ ref, int64_t nx,
                                                           int64_t ny, int ndim, double g0,
@@ -259,7 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             cpx<T> a, b;
-            load_pair<T>(X, nsites, m, site, a, b);
+            if (RESIDENT) load_pair<T>(X, nsites, m, site, a, b); else load_pair_abi<T>(X, nsites, m, site, a, b);
             const cpx<double> ad = {double(a.re), double(a.im)}, bd = {double(b.re), double(b.im)};
             const double pm = norm2(ad) + norm2(bd);
             acc[OBS_NORM_QUBIT] += pm;
@@ -286,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
                 cpx<T> a, b;
-                load_pair<T>(X, nsites, m, sn, a, b);
+                if (RESIDENT) load_pair<T>(X, nsites, m, sn, a, b); else load_pair_abi<T>(X, nsites, m, sn, a, b);
                 const cpx<double> pn = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
                 grad += norm2(pn - psi[m]);
             }
@@ -300,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
                 cpx<T> a, b;
-                load_pair<T>(ref, nsites, m, site, a, b);
+                load_pair_abi<T>(ref, nsites, m, site, a, b);  // reference states are caller buffers (ABI layout)
                 const cpx<double> r = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
                 const cpx<double> ov = cmulc(psi[m], r);
                 acc[OBS_OVERLAP_RE] += ov.re;
@@ -400,7 +425,7 @@ template <class T>
 qlga_status launch_potential(qlga_handle* h, void* buf, double delta) {
     const int64_t n = nsites_of(h->cfg);
     k_potential<T, std::is_same<T, float>::value><<<grid_for(n), kThreads, 0, h->stream>>>(
-        static_cast<T*>(buf), n, pot_params(h->cfg, delta), h->status);
+        static_cast<T*>(buf), n, PotConst<T>(pot_params(h->cfg, delta)), h->status);
     QLGA_CUDA(cudaGetLastError(), "k_potential launch");
     h->launches += 1;
     return QLGA_OK;
@@ -411,7 +436,7 @@ qlga_status launch_axis_t(qlga_handle* h, const void* in, void* out, int axis) {
     const int64_t n = nsites_of(h->cfg);
     k_kinetic_axis<T, V, POT><<<grid_for(n), kThreads, 0, h->stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), h->cfg.nx, h->cfg.ny, axis,
-        pot_params(h->cfg, 1.0), h->status);
+        PotConst<T>(pot_params(h->cfg, 1.0)), h->status);
     QLGA_CUDA(cudaGetLastError(), "k_kinetic_axis launch");
     h->launches += 1;
     return QLGA_OK;
@@ -457,7 +482,7 @@ qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, b
     if (h->cfg.ndim == 1) return launch_axis(h, in, out, 0, pot);
     if (pot && h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
         if (step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx,
-                              h->cfg.ny, h->cfg.kinetic_variant, pot_params(h->cfg, 1.0), h->status,
+                              h->cfg.ny, h->cfg.kinetic_variant, PotConst<float>(pot_params(h->cfg, 1.0)), h->status,
                               h->stream))
             return cuda_fail(cudaGetLastError(), "step2d launch");
         h->launches += 1;
@@ -466,6 +491,26 @@ qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, b
     qlga_status s = launch_axis(h, in, mid, 0, false);
     if (s != QLGA_OK) return s;
     return launch_axis(h, mid, out, 1, pot);
+}
+
+// ABI layout <-> resident layout (see qlga_device.cuh); src may equal dst.
+qlga_status launch_convert(qlga_handle* h, const void* src, void* dst, bool to_resident) {
+    const int64_t np = 5 * nsites_of(h->cfg);
+    const int g = grid_for(np);
+    if (h->cfg.precision == 32) {
+        if (to_resident)
+            k_convert_layout<float, true><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(src), static_cast<float*>(dst), np);
+        else
+            k_convert_layout<float, false><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(src), static_cast<float*>(dst), np);
+    } else {
+        if (to_resident)
+            k_convert_layout<double, true><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(src), static_cast<double*>(dst), np);
+        else
+            k_convert_layout<double, false><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(src), static_cast<double*>(dst), np);
+    }
+    QLGA_CUDA(cudaGetLastError(), "k_convert_layout launch");
+    h->launches += 1;
+    return QLGA_OK;
 }
 
 // Make the buffer hold the true state (pending K applied).
@@ -560,12 +605,12 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
     double* result = scratch + size_t(kNoAllocRows) * OBS_COUNT;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cfg->precision == 32)
-        k_observables<float><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(state_device),
+        k_observables<float, false><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(state_device),
                                                           static_cast<const float*>(ref_state_device),
                                                           cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
                                                           cfg->g2, scratch);
     else
-        k_observables<double><<<blocks, kThreads, 0, st>>>(static_cast<const double*>(state_device),
+        k_observables<double, false><<<blocks, kThreads, 0, st>>>(static_cast<const double*>(state_device),
                                                            static_cast<const double*>(ref_state_device),
                                                            cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
                                                            cfg->g2, scratch);
@@ -693,8 +738,13 @@ qlga_status qlga_load_state(qlga_handle* h, const void* src, int where) {
     if (!h || !src) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
     if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
     const size_t nb = state_bytes_of(h->cfg);
-    QLGA_CUDA(cudaMemcpyAsync(h->X[h->cur], src, nb, where == QLGA_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream),
-              "qlga_load_state copy");
+    const void* dev_src = src;
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaMemcpyAsync(h->tmp, src, nb, cudaMemcpyHostToDevice, h->stream), "qlga_load_state copy");
+        dev_src = h->tmp;
+    }
+    qlga_status s = launch_convert(h, dev_src, h->X[h->cur], true);
+    if (s != QLGA_OK) return s;
     if (where == QLGA_HOST) QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_load_state sync");
     h->pending_k = false;
     h->step = 0;
@@ -729,13 +779,13 @@ qlga_status qlga_get_state(qlga_handle* h, void* dst, int where) {
     const void* view = nullptr;
     qlga_status s = true_state_view(h, &view);
     if (s != QLGA_OK) return s;
-    QLGA_CUDA(cudaMemcpyAsync(dst, view, state_bytes_of(h->cfg), where == QLGA_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream),
-              "qlga_get_state copy");
-    if (where == QLGA_HOST) {
-        QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_get_state sync");
-        return check_status_word(h);
-    }
-    return QLGA_OK;
+    if (where == QLGA_DEVICE) return launch_convert(h, view, dst, false);
+    // host: convert into the work buffer (in place when the view already is it), then copy
+    s = launch_convert(h, view, h->tmp, false);
+    if (s != QLGA_OK) return s;
+    QLGA_CUDA(cudaMemcpyAsync(dst, h->tmp, state_bytes_of(h->cfg), cudaMemcpyDeviceToHost, h->stream), "qlga_get_state copy");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_get_state sync");
+    return check_status_word(h);
 }
 
 qlga_status qlga_step(qlga_handle* h, int64_t n) {
@@ -797,10 +847,10 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
     const int64_t n = nsites_of(h->cfg);
     const int blocks = grid_for(n, kObsMaxBlocks);
     if (h->cfg.precision == 32)
-        k_observables<float><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
+        k_observables<float, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
                                                                  h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
     else
-        k_observables<double><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
+        k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
                                                                   h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch");
     k_reduce_partials<<<1, 32, 0, h->stream>>>(h->partials, blocks, h->obs_dev);

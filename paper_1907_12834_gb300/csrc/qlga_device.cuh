@@ -1,9 +1,11 @@
 // qlga_device.cuh -- device building blocks of the spin-2 QLGA step (arXiv:1907.12834).
 //
 // Conventions shared by every kernel of the library:
-//  * State: 5 planes (m = +2..-2) of ny*nx sites, x fastest; a site is the qubit pair of that
-//    level as (a.re, a.im, b.re, b.im).  One float4 (FP32) or two double2 (FP64) per site and
-//    plane, so a warp reading 32 consecutive sites of a plane reads 512 or 1024 contiguous bytes.
+//  * Resident state: 5 planes (m = +2..-2) of ny*nx sites, x fastest; a site is the qubit pair
+//    of that level as (a.re, a.im, bt.re, bt.im) with bt = i*b.  One float4 (FP32) or two double2
+//    (FP64) per site and plane, so a warp reading 32 consecutive sites of a plane reads 512 or
+//    1024 contiguous bytes.  The C ABI's layout (a.re, a.im, b.re, b.im) is converted on load and
+//    read-out only; SiteIO / load_pair return (a, b).
 //  * Inside the kinetic operator the pair is carried as (a, bt) with bt = i*b.  In that basis the
 //    collide C = 1/2 [[1-i, 1+i], [1+i, 1-i]] of a kinetic block (Sec. VII.B) becomes the scalar
 //    (1-i)/2 times the real matrix [[1, 1], [-1, 1]], so a collide costs four real additions per
@@ -67,14 +69,14 @@ struct SiteIO<float> {
         for (int m = 0; m < 5; ++m) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(X) + m * nsites + site);
             a[m] = {v.x, v.y};
-            b[m] = {v.z, v.w};
+            b[m] = {v.w, -v.z};  // b = -i bt
         }
     }
     static __device__ __forceinline__ void store(float* X, int64_t nsites, int64_t site,
                                                  const cpx<float> a[5], const cpx<float> b[5]) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m)
-            reinterpret_cast<float4*>(X)[m * nsites + site] = make_float4(a[m].re, a[m].im, b[m].re, b[m].im);
+        for (int m = 0; m < 5; ++m)  // bt = i b
+            reinterpret_cast<float4*>(X)[m * nsites + site] = make_float4(a[m].re, a[m].im, -b[m].im, b[m].re);
     }
 };
 
@@ -87,7 +89,7 @@ struct SiteIO<double> {
             const double2* p = reinterpret_cast<const double2*>(X) + 2 * (m * nsites + site);
             const double2 va = __ldg(p), vb = __ldg(p + 1);
             a[m] = {va.x, va.y};
-            b[m] = {vb.x, vb.y};
+            b[m] = {vb.y, -vb.x};
         }
     }
     static __device__ __forceinline__ void store(double* X, int64_t nsites, int64_t site,
@@ -96,7 +98,7 @@ struct SiteIO<double> {
         for (int m = 0; m < 5; ++m) {
             double2* p = reinterpret_cast<double2*>(X) + 2 * (m * nsites + site);
             p[0] = make_double2(a[m].re, a[m].im);
-            p[1] = make_double2(b[m].re, b[m].im);
+            p[1] = make_double2(-b[m].im, b[m].re);
         }
     }
 };
@@ -209,7 +211,7 @@ struct PotParams {
     double g0, g1, g2, delta;
 };
 
-// Per-thread constants of the potential, converted once per kernel from PotParams.
+// Constants of the potential in the arithmetic type, computed on the host from PotParams.
 template <class T>
 struct PotConst {
     T cphase;  // delta (g0 + g2/25): e^{-i delta c} with c = (g0 + g2/25) rho
@@ -218,7 +220,8 @@ struct PotConst {
     T e0, e1;  // delta g1, delta g1 sqrt(3/2): off-diagonal spin entries per unit F_+
     T R;       // delta g2 / 5: singlet rank-one term
     T b1, b2;  // 2 |g1| delta, (4/25) |g2| delta: beta = b1 |F| + b2 rho
-    __device__ __forceinline__ explicit PotConst(const PotParams& P) {
+    PotConst() = default;
+    __host__ __device__ explicit PotConst(const PotParams& P) {
         cphase = T(P.delta * (P.g0 + P.g2 / 25.0));
         dz = T(P.delta * P.g1);
         dr = T(P.delta * P.g2 / 25.0);
@@ -252,9 +255,15 @@ template <>
 struct TaylorTol<double> {
     static constexpr double value = 1.1102230246251565e-16;  // 2^-53
 };
+// FP32: bound on the truncation relative to the site amplitude, per step.  1e-8 sits below the
+// FP32 rounding of one step (~1e-7): tightening it to 1e-9 left the FP32-vs-FP64 drift of the 1D
+// and 2D workloads unchanged while costing one more Taylor term in the vortex background.
+#ifndef QLGA_F32_TAYLOR_TOL
+#define QLGA_F32_TAYLOR_TOL 1e-8f
+#endif
 template <>
 struct TaylorTol<float> {
-    static constexpr float value = 1e-9f;  // keeps the systematic truncation far below FP32 rounding
+    static constexpr float value = QLGA_F32_TAYLOR_TOL;
 };
 
 // e^{-i x} parts.  FP32: for |x| <= 1/2 the Taylor series of sin and cos to x^9 / x^10
@@ -297,10 +306,11 @@ struct WOp {
     T R;           // delta g2 / 5 (times inv_sigma2)
 
     __device__ __forceinline__ void apply(const cpx<T> x[5], cpx<T> y[5]) const {
-        cpx<T> t = cmul(u[0], x[0]);
-#pragma unroll
-        for (int j = 1; j < 5; ++j) t = cfma(u[j], x[j], t);
-        t = R * t;
+        cpx<T> t0 = cmul(u[0], x[0]), t1 = cmul(u[1], x[1]);
+        t0 = cfma(u[2], x[2], t0);
+        t1 = cfma(u[3], x[3], t1);
+        t0 = cfma(u[4], x[4], t0);
+        const cpx<T> t = R * (t0 + t1);
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             // D_i x_i + t * conj(u_i)
@@ -317,15 +327,34 @@ struct WOp {
 
 // v <- exp(-i delta W) x by the degree-K Taylor polynomial (Horner form; K is warp-uniform)
 template <class T>
-__device__ __forceinline__ void taylor_apply(const WOp<T>& W, const cpx<T> x[5], cpx<T> v[5], int K) {
+__device__ __forceinline__ void horner_step(const cpx<T> x[5], const cpx<T> w[5], cpx<T> v[5], T ik) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) v[i] = x[i];
-    for (int k = K; k >= 1; --k) {
+    for (int i = 0; i < 5; ++i) v[i] = {fma(ik, w[i].im, x[i].re), fma(-ik, w[i].re, x[i].im)};
+}
+
+// vp <- exp(-i delta W) xp (degree K) and vd <- exp(-i delta W) xd (degree Kd <= K).  Both
+// Horner recursions run in one loop so their independent matrix-vector products interleave.
+template <class T>
+__device__ __forceinline__ void taylor_apply2(const WOp<T>& W, const cpx<T> xp[5], cpx<T> vp[5],
+                                              const cpx<T> xd[5], cpx<T> vd[5], int K, int Kd) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        vp[i] = xp[i];
+        vd[i] = xd[i];
+    }
+    int k = K;
+    for (; k > Kd; --k) {
         cpx<T> w[5];
-        W.apply(v, w);
+        W.apply(vp, w);
+        horner_step(xp, w, vp, inv_k(k, T(0)));
+    }
+    for (; k >= 1; --k) {
+        cpx<T> wp[5], wd[5];
+        W.apply(vp, wp);
+        W.apply(vd, wd);
         const T ik = inv_k(k, T(0));
-#pragma unroll
-        for (int i = 0; i < 5; ++i) v[i] = {fma(ik, w[i].im, x[i].re), fma(-ik, w[i].re, x[i].im)};
+        horner_step(xp, wp, vp, ik);
+        horner_step(xd, wd, vd, ik);
     }
 }
 
@@ -389,8 +418,7 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
     W.u[4] = psi[0];
     W.R = C.R * inv_sigma2;
     cpx<T> vp[5], vd[5];
-    taylor_apply(W, psi, vp, K);
-    taylor_apply(W, d, vd, Kd);
+    taylor_apply2(W, psi, vp, d, vd, K, Kd);
     T sn, cs;
     sin_cos(C.cphase * rho, &sn, &cs);
     const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)

@@ -43,33 +43,67 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Packed FP32 pairs: a complex number (re, im) is one float2 and every kinetic coefficient is
+// real, so the stencil and the collides act on both halves with one f32x2 instruction.
+// STYLE selects how integer coefficients are issued: 0 = f32x2 with coefficient pairs,
+// 1 = f32x2 add / sub for +-1 and scalar FFMA with an immediate for larger coefficients,
+// 2 = scalar FP32 only.
+#ifndef QLGA_STEP2D_STYLE
+#define QLGA_STEP2D_STYLE 1
+#endif
+
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+template <int STYLE>
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) {
+    if (STYLE == 2) return make_float2(a.x + b.x, a.y + b.y);
+    return __fadd2_rn(a, b);
+}
+template <int STYLE>
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+    if (STYLE == 2) return make_float2(a.x - b.x, a.y - b.y);
+    if (STYLE == 1) return f2_sub(a, b);
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+template <int STYLE>
+__device__ __forceinline__ float2 p_fma(float c, float2 x, float2 acc) {
+    if (STYLE == 0) return __ffma2_rn(make_float2(c, c), x, acc);
+    return make_float2(fmaf(c, x.x, acc.x), fmaf(c, x.y, acc.y));
+}
+
 // Streaming state of one kinetic block for one level: the unshifted qubit of the first collide
 // from the previous row (yo) and the shifted qubit of the second collide from the previous row
 // (wc), both in the (a, bt = i b) basis.
 struct BlockState {
-    cpx<float> yo, wc;
+    float2 yo, wc;
 };
 
 // One block I'_c on the stream: input row n (xa, xbt) -> output row n-1, in place.
 // c = 1 shifts bt (qubit 2), c = 0 shifts a (qubit 1).  FIRST selects the first collide:
 // 0 = [[1, 1], [-1, 1]] (K1), 1 = [[1, -1], [1, 1]] (K2); the second collide is always
 // [[1, 1], [-1, 1]].
-template <int C, int FIRST>
-__device__ __forceinline__ void stream_block(cpx<float>& xa, cpx<float>& xbt, BlockState& s) {
-    cpx<float> ya, ybt;
+template <int C, int FIRST, int STYLE>
+__device__ __forceinline__ void stream_block(float2& xa, float2& xbt, BlockState& s) {
+    float2 ya, ybt;
     if (FIRST == 0) {
-        ya = xa + xbt;
-        ybt = xbt - xa;
+        ya = p_add<STYLE>(xa, xbt);
+        ybt = p_sub<STYLE>(xbt, xa);
     } else {
-        ya = xa - xbt;
-        ybt = xa + xbt;
+        ya = p_sub<STYLE>(xa, xbt);
+        ybt = p_add<STYLE>(xa, xbt);
     }
     // Z(n-1): shifted qubit from the current row (S^T: c(j) <- c(j+1)), other qubit from the
     // previous row
-    const cpx<float> za = C == 0 ? ya : s.yo;
-    const cpx<float> zbt = C == 0 ? s.yo : ybt;
+    const float2 za = C == 0 ? ya : s.yo;
+    const float2 zbt = C == 0 ? s.yo : ybt;
     s.yo = C == 0 ? ybt : ya;
-    const cpx<float> wa = za + zbt, wbt = zbt - za;
+    const float2 wa = p_add<STYLE>(za, zbt), wbt = p_sub<STYLE>(zbt, za);
     // output row n-1: shifted qubit from W(n-2) (S: c(j) <- c(j-1)), other from W(n-1)
     if (C == 0) {
         xa = s.wc;
@@ -82,13 +116,30 @@ __device__ __forceinline__ void stream_block(cpx<float>& xa, cpx<float>& xbt, Bl
     }
 }
 
-template <int VARIANT>
+// acc += c * x for a compile-time integer coefficient (0: nothing, +-1: add / subtract)
+template <int COEF, int STYLE>
+__device__ __forceinline__ float2 tap(float2 x, float2 acc) {
+    if (COEF == 0) return acc;
+    if (COEF == 1) return p_add<STYLE>(acc, x);
+    if (COEF == -1) return p_sub<STYLE>(acc, x);
+    return p_fma<STYLE>(float(COEF), x, acc);
+}
+
+template <int VARIANT, int K, int STYLE>
+__device__ __forceinline__ void stencil_tap(const float4 v, float2& xa, float2& xbt) {
+    constexpr KinStencil S = kStencil[VARIANT];
+    const float2 a = make_float2(v.x, v.y), bt = make_float2(v.z, v.w);
+    xa = tap<S.g[0][0][K], STYLE>(a, xa);
+    xa = tap<S.g[0][1][K], STYLE>(bt, xa);
+    xbt = tap<S.g[1][0][K], STYLE>(a, xbt);
+    xbt = tap<S.g[1][1][K], STYLE>(bt, xbt);
+}
+
+template <int VARIANT, int STYLE = QLGA_STEP2D_STYLE>
 __global__ void __launch_bounds__(kStep2dW, 3)
     k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
-                 PotParams P, unsigned* status) {
+                 PotConst<float> PC, unsigned* status) {
     extern __shared__ float4 ring[];  // [kStages][5][kRowSites]
-    constexpr KinStencil S = kStencil[VARIANT];
-    const PotConst<float> PC(P);
     const int t = threadIdx.x;
     const int strips = nx / kStep2dW;
     const int strip = blockIdx.x % strips;
@@ -131,7 +182,7 @@ __global__ void __launch_bounds__(kStep2dW, 3)
 #pragma unroll
     for (int m = 0; m < 5; ++m)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) st[m][k] = {{0.f, 0.f}, {0.f, 0.f}};
+        for (int k = 0; k < 4; ++k) st[m][k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
     const float inv_sigma2 = 1.0f / 65536.0f;  // sigma = 256
     const float out_scale = 0.5f / 256.0f;
@@ -147,33 +198,34 @@ __global__ void __launch_bounds__(kStep2dW, 3)
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             // x axis: nine-point stencil (x16, unnormalised) in the (a, bt) basis
-            cpx<float> xa = {0.f, 0.f}, xbt = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const float4 v = row[m * kStep2dRowSites + t + k];
-                const cpx<float> a = {v.x, v.y};
-                const cpx<float> bt = {-v.w, v.z};
-                const float caa = float(S.g[0][0][k]), cab = float(S.g[0][1][k]);
-                const float cba = float(S.g[1][0][k]), cbb = float(S.g[1][1][k]);
-                xa.re = fmaf(caa, a.re, fmaf(cab, bt.re, xa.re));
-                xa.im = fmaf(caa, a.im, fmaf(cab, bt.im, xa.im));
-                xbt.re = fmaf(cba, a.re, fmaf(cbb, bt.re, xbt.re));
-                xbt.im = fmaf(cba, a.im, fmaf(cbb, bt.im, xbt.im));
-            }
+            const float4* p = row + m * kStep2dRowSites + t;
+            float2 xa = make_float2(0.f, 0.f), xbt = make_float2(0.f, 0.f);
+            float2 ya = make_float2(0.f, 0.f), ybt = make_float2(0.f, 0.f);  // second accumulators
+            stencil_tap<VARIANT, 0, STYLE>(p[0], xa, xbt);
+            stencil_tap<VARIANT, 1, STYLE>(p[1], ya, ybt);
+            stencil_tap<VARIANT, 2, STYLE>(p[2], xa, xbt);
+            stencil_tap<VARIANT, 3, STYLE>(p[3], ya, ybt);
+            stencil_tap<VARIANT, 4, STYLE>(p[4], xa, xbt);
+            stencil_tap<VARIANT, 5, STYLE>(p[5], ya, ybt);
+            stencil_tap<VARIANT, 6, STYLE>(p[6], xa, xbt);
+            stencil_tap<VARIANT, 7, STYLE>(p[7], ya, ybt);
+            stencil_tap<VARIANT, 8, STYLE>(p[8], xa, xbt);
+            xa = p_add<STYLE>(xa, ya);
+            xbt = p_add<STYLE>(xbt, ybt);
             // y axis: I'_2 I'_2 then I'_1 I'_1 as a streaming pipeline (x16, unnormalised)
-            stream_block<1, VARIANT>(xa, xbt, st[m][0]);
-            stream_block<1, VARIANT>(xa, xbt, st[m][1]);
-            stream_block<0, VARIANT>(xa, xbt, st[m][2]);
-            stream_block<0, VARIANT>(xa, xbt, st[m][3]);
-            oa[m] = xa;
-            ob[m] = {xbt.im, -xbt.re};  // b = -i bt
+            stream_block<1, VARIANT, STYLE>(xa, xbt, st[m][0]);
+            stream_block<1, VARIANT, STYLE>(xa, xbt, st[m][1]);
+            stream_block<0, VARIANT, STYLE>(xa, xbt, st[m][2]);
+            stream_block<0, VARIANT, STYLE>(xa, xbt, st[m][3]);
+            oa[m] = {xa.x, xa.y};
+            ob[m] = {xbt.y, -xbt.x};  // b = -i bt
         }
         if (r >= 8) {  // pipeline full: this is output row y_begin + r - 8
             potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
             const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + t;
 #pragma unroll
-            for (int m = 0; m < 5; ++m)
-                out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, ob[m].re, ob[m].im);
+            for (int m = 0; m < 5; ++m)  // resident layout: (a, bt = i b)
+                out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
         }
     }
     cp_async_wait<0>();
@@ -195,7 +247,7 @@ inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
 
 // Returns 0 on success (errors are left in cudaGetLastError()).
 inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant,
-                             PotParams P, unsigned* status, cudaStream_t stream) {
+                             PotConst<float> PC, unsigned* status, cudaStream_t stream) {
     static int sms = 0, per_sm[2] = {0, 0};
     if (sms == 0) {
         int dev = 0;
@@ -209,9 +261,9 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
     const int chunks = step2d_chunks(nx, ny, sms, per_sm[variant] > 0 ? per_sm[variant] : 1);
     const int grid = int(nx / kStep2dW) * chunks;
     if (variant == 0)
-        k_step2d_f32<0><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, P, status);
+        k_step2d_f32<0><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
     else
-        k_step2d_f32<1><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, P, status);
+        k_step2d_f32<1><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
     return cudaPeekAtLastError() != cudaSuccess;
 }
 

@@ -264,7 +264,31 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Per-site observable terms in FP64, block sums into partials[block][OBS_COUNT].
+// Per-thread accumulator: FP64 for an FP64 state; compensated (Kahan) FP32 for an FP32 state,
+// whose per-site terms carry FP32 rounding anyway.  Block and grid sums are FP64.
+template <class T>
+struct ThreadSum;
+template <>
+struct ThreadSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct ThreadSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
+
+// Per-site observable terms in the state's precision, block sums (FP64) into
+// partials[block][OBS_COUNT].  X_RESIDENT: X is in the resident layout (else the ABI layout);
+// the reference state is always a caller buffer in the ABI layout.
 template <class T, bool RESIDENT>
 __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ X,
                                                           const T* __restrict__ ref, int64_t nx,
@@ -272,38 +296,36 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
                                                           double g1, double g2,
                                                           double* __restrict__ partials) {
     const int64_t nsites = nx * ny;
-    double acc[OBS_COUNT];
-#pragma unroll
-    for (int k = 0; k < OBS_COUNT; ++k) acc[k] = 0.0;
-    const double r32 = 1.2247448713915890491;
+    ThreadSum<T> acc[OBS_COUNT];
+    const T r32 = T(1.2247448713915890491);
+    const T hg0 = T(0.5 * g0), hg1 = T(0.5 * g1), tg2 = T(0.1 * g2);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
         const int64_t x = site % nx, y = site / nx;
-        cpx<double> psi[5];
-        double rho = 0.0;
+        cpx<T> psi[5];
+        T rho = T(0);
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             cpx<T> a, b;
             if (RESIDENT) load_pair<T>(X, nsites, m, site, a, b); else load_pair_abi<T>(X, nsites, m, site, a, b);
-            const cpx<double> ad = {double(a.re), double(a.im)}, bd = {double(b.re), double(b.im)};
-            const double pm = norm2(ad) + norm2(bd);
-            acc[OBS_NORM_QUBIT] += pm;
-            acc[OBS_POP0 + m] += pm;
-            psi[m] = ad + bd;
+            const T pm = norm2(a) + norm2(b);
+            acc[OBS_NORM_QUBIT].add(pm);
+            acc[OBS_POP0 + m].add(pm);
+            psi[m] = a + b;
             rho += norm2(psi[m]);
         }
-        acc[OBS_NORM_BOSON] += rho;
+        acc[OBS_NORM_BOSON].add(rho);
         // F_z, F_+ = psi^dagger f_+ psi (f_+ = f_x + i f_y): |F|^2 = F_z^2 + |F_+|^2
-        const double Fz = 2.0 * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
-        cpx<double> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
-        const cpx<double> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
-        Fp = {2.0 * (Fp.re + r32 * mid.re), 2.0 * (Fp.im + r32 * mid.im)};
-        const double F2 = Fz * Fz + norm2(Fp);
+        const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
+        cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
+        const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
+        Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
+        const T F2 = Fz * Fz + norm2(Fp);
         // theta = psi^T J psi = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2
-        const cpx<double> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
-        const cpx<double> th = {2.0 * (t1.re - t2.re) + t3.re, 2.0 * (t1.im - t2.im) + t3.im};
-        const double th2 = norm2(th);
-        double grad = 0.0;
+        const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
+        const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+        const T th2 = norm2(th);
+        T grad = T(0);
         for (int ax = 0; ax < ndim; ++ax) {
             const int64_t xn = ax == 0 ? (x + 1 == nx ? 0 : x + 1) : x;
             const int64_t yn = ax == 1 ? (y + 1 == ny ? 0 : y + 1) : y;
@@ -312,32 +334,31 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
             for (int m = 0; m < 5; ++m) {
                 cpx<T> a, b;
                 if (RESIDENT) load_pair<T>(X, nsites, m, sn, a, b); else load_pair_abi<T>(X, nsites, m, sn, a, b);
-                const cpx<double> pn = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
-                grad += norm2(pn - psi[m]);
+                grad += norm2((a + b) - psi[m]);
             }
         }
-        acc[OBS_ENERGY] += grad + 0.5 * g0 * rho * rho + 0.5 * g1 * F2 + 0.1 * g2 * th2;
-        acc[OBS_SINGLET_RE] += th.re * 0.44721359549995793928;  // 1/sqrt(5)
-        acc[OBS_SINGLET_IM] += th.im * 0.44721359549995793928;
-        acc[OBS_THETA2] += th2;
-        acc[OBS_RHO2] += rho * rho;
+        acc[OBS_ENERGY].add(grad + hg0 * rho * rho + hg1 * F2 + tg2 * th2);
+        acc[OBS_SINGLET_RE].add(th.re * T(0.44721359549995793928));  // 1/sqrt(5)
+        acc[OBS_SINGLET_IM].add(th.im * T(0.44721359549995793928));
+        acc[OBS_THETA2].add(th2);
+        acc[OBS_RHO2].add(rho * rho);
         if (ref) {
+            cpx<T> ov = {T(0), T(0)};
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
                 cpx<T> a, b;
                 load_pair_abi<T>(ref, nsites, m, site, a, b);  // reference states are caller buffers (ABI layout)
-                const cpx<double> r = {double(a.re) + double(b.re), double(a.im) + double(b.im)};
-                const cpx<double> ov = cmulc(psi[m], r);
-                acc[OBS_OVERLAP_RE] += ov.re;
-                acc[OBS_OVERLAP_IM] += ov.im;
+                ov = cfmac(psi[m], a + b, ov);
             }
+            acc[OBS_OVERLAP_RE].add(ov.re);
+            acc[OBS_OVERLAP_IM].add(ov.im);
         }
     }
     __shared__ double sh[kThreads / 32][OBS_COUNT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < OBS_COUNT; ++k) {
-        const double v = warp_sum(acc[k]);
+        const double v = warp_sum(acc[k].value());
         if (lane == 0) sh[warp][k] = v;
     }
     __syncthreads();
@@ -348,19 +369,42 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
     }
 }
 
-// out[k] = Neumaier-compensated sum of partials[b][k] over blocks, in a fixed order.
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks,
-                                  double* __restrict__ out) {
-    const int k = threadIdx.x;
-    if (k >= OBS_COUNT) return;
+// Neumaier-compensated running sum.
+struct CompSum {
     double s = 0.0, c = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        const double v = partials[int64_t(b) * OBS_COUNT + k];
+    __device__ __forceinline__ void add(double v) {
         const double t = s + v;
         c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
         s = t;
     }
-    out[k] = s + c;
+};
+
+// out[k] = compensated sum of partials[b][k] over blocks, in a fixed order: warp k reduces
+// quantity k, lane l takes blocks l, l+32, ..., then the 32 (sum, compensation) pairs combine
+// in a fixed butterfly.  Launch with OBS_COUNT warps.
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks,
+                                  double* __restrict__ out) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= OBS_COUNT) return;
+    CompSum cs;
+    for (int b = lane; b < nblocks; b += 32) cs.add(partials[int64_t(b) * OBS_COUNT + k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, cs.s, o);
+        const double oc = __shfl_xor_sync(0xffffffffu, cs.c, o);
+        // both lanes of a pair compute the same combination (lower lane's terms first)
+        CompSum m;
+        if (lane & o) {
+            m.add(os);
+            m.add(cs.s);
+        } else {
+            m.add(cs.s);
+            m.add(os);
+        }
+        m.c += (lane & o) ? (oc + cs.c) : (cs.c + oc);
+        cs = m;
+    }
+    if (lane == 0) out[k] = cs.s + cs.c;
 }
 
 }  // namespace qlga
@@ -480,10 +524,10 @@ qlga_status launch_block(qlga_handle* h, const void* in, void* out, int axis, in
 // x pass.  With pot, U follows the last axis (the fused step).
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
     if (h->cfg.ndim == 1) return launch_axis(h, in, out, 0, pot);
-    if (pot && h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
+    if (h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
         if (step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx,
-                              h->cfg.ny, h->cfg.kinetic_variant, PotConst<float>(pot_params(h->cfg, 1.0)), h->status,
-                              h->stream))
+                              h->cfg.ny, h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)),
+                              h->status, h->stream))
             return cuda_fail(cudaGetLastError(), "step2d launch");
         h->launches += 1;
         return QLGA_OK;
@@ -615,7 +659,7 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
                                                            cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
                                                            cfg->g2, scratch);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch (no-alloc)");
-    k_reduce_partials<<<1, 32, 0, st>>>(scratch, blocks, result);
+    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, st>>>(scratch, blocks, result);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (no-alloc)");
     double o[OBS_COUNT];
     QLGA_CUDA(cudaMemcpyAsync(o, result, sizeof(o), cudaMemcpyDeviceToHost, st), "no-alloc observables copy");
@@ -853,7 +897,7 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
         k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
                                                                   h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch");
-    k_reduce_partials<<<1, 32, 0, h->stream>>>(h->partials, blocks, h->obs_dev);
+    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, h->stream>>>(h->partials, blocks, h->obs_dev);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
     h->launches += 2;
     double o[OBS_COUNT];

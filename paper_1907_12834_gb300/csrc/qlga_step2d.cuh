@@ -135,7 +135,8 @@ __device__ __forceinline__ void stencil_tap(const float4 v, float2& xa, float2& 
     xbt = tap<S.g[1][1][K], STYLE>(bt, xbt);
 }
 
-template <int VARIANT, int STYLE = QLGA_STEP2D_STYLE>
+// POT = false: the kinetic operator alone (out = K X), used to read out a state held pending K.
+template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
 __global__ void __launch_bounds__(kStep2dW, 3)
     k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
                  PotConst<float> PC, unsigned* status) {
@@ -221,7 +222,16 @@ __global__ void __launch_bounds__(kStep2dW, 3)
             ob[m] = {xbt.y, -xbt.x};  // b = -i bt
         }
         if (r >= 8) {  // pipeline full: this is output row y_begin + r - 8
-            potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
+            if (POT) {
+                potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
+            } else {
+                const float s = 1.0f / 256.0f;  // exact: undo the unnormalised collides
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    oa[m] = s * oa[m];
+                    ob[m] = s * ob[m];
+                }
+            }
             const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + t;
 #pragma unroll
             for (int m = 0; m < 5; ++m)  // resident layout: (a, bt = i b)
@@ -245,25 +255,30 @@ inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
     return int(chunks);
 }
 
-// Returns 0 on success (errors are left in cudaGetLastError()).
-inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant,
+// Returns 0 on success (errors are left in cudaGetLastError()).  pot = false applies the kinetic
+// operator alone.
+inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant, bool pot,
                              PotConst<float> PC, unsigned* status, cudaStream_t stream) {
-    static int sms = 0, per_sm[2] = {0, 0};
+    static int sms = 0, per_sm = 0;
     if (sms == 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 1;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_step2d_f32<0>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_step2d_f32<1>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step2d_f32<0, true>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
     }
-    const int chunks = step2d_chunks(nx, ny, sms, per_sm[variant] > 0 ? per_sm[variant] : 1);
+    const int chunks = step2d_chunks(nx, ny, sms, per_sm > 0 ? per_sm : 1);
     const int grid = int(nx / kStep2dW) * chunks;
-    if (variant == 0)
-        k_step2d_f32<0><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-    else
-        k_step2d_f32<1><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    if (variant == 0) {
+        if (pot) k_step2d_f32<0, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<0, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    } else {
+        if (pot) k_step2d_f32<1, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<1, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    }
     return cudaPeekAtLastError() != cudaSuccess;
 }
 

@@ -172,13 +172,15 @@ def test_observables(precision, ndim, nx, ny):
     cfg = oracle.make_cfg(ndim, nx, ny, *g)
     w = oracle.observables(np.ascontiguousarray(st_c, dtype=np.float64), cfg,
                            ref=np.ascontiguousarray(ref_st.astype(lat.dtype), dtype=np.float64))
-    tol = 1e-12
+    # FP64 state: FP64 terms and sums.  FP32 state: per-site terms in FP32 (a few ulp, 6e-8 each),
+    # compensated per-thread sums, FP64 across threads -> relative error ~1e-7 of the scale.
+    tol = 1e-12 if precision == 64 else 1e-6
     scale = w["norm_qubit"]
     for k in ("norm_qubit", "norm_boson", "magnetisation", "energy", "singlet_re", "singlet_im",
               "overlap_re", "overlap_im"):
         assert abs(o[k] - w[k]) <= tol * scale, k
     np.testing.assert_allclose(o["pop"], w["pop"], rtol=0, atol=tol * scale)
-    assert abs(o["singlet_fraction"] - w["singlet_fraction"]) <= 1e-10
+    assert abs(o["singlet_fraction"] - w["singlet_fraction"]) <= (1e-10 if precision == 64 else 1e-6)
 
 
 # ------------------------------------------------------------------ the paper's workloads
@@ -199,6 +201,27 @@ def test_config0_bright_soliton_full_run_fp64():
     lat.close()
     assert abs(o["norm_qubit"] - o0["norm_qubit"]) <= 1e-12 * o0["norm_qubit"]
     assert abs(o["magnetisation"] - o0["magnetisation"]) <= 1e-12 * o0["norm_qubit"]
+
+
+def test_config0_bright_soliton_full_run_fp32():
+    """Config 0 in FP32 (FP64 reductions) over its full 2000 steps: within 1e-4 of the FP64
+    oracle (measured ~1e-5; the dynamics of this single-level soliton is stable)."""
+    w = I.config0()
+    st = w.state.astype(np.float32)
+    got = run_gpu(st, 1, w.nx, 1, w.g, w.steps, 32)
+    ref = run_oracle(st, 1, w.nx, 1, w.g, w.steps)
+    assert rel_l2(got, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("couplings", [(1.0, -0.5, 0.2), (1.0, 0.8, -0.6)])
+def test_config1_scattering_2000_steps_fp64(couplings):
+    """Config 1 at full size, FP64, 2000 of its 20000 steps: 1e-11.  (Over the full 20000 steps
+    the stable coupling set stays at ~1e-11 and the integrable one grows to ~1e-9 through the
+    dynamics' own amplification of rounding differences.)"""
+    w = I.config1(couplings=couplings)
+    got = run_gpu(w.state, 1, w.nx, 1, w.g, 2000, 64)
+    ref = run_oracle(w.state, 1, w.nx, 1, w.g, 2000)
+    assert rel_l2(got, ref) <= 1e-11
 
 
 @pytest.mark.parametrize("couplings", [(1.0, -0.5, 0.2), (1.0, 0.8, -0.6)])

@@ -283,3 +283,4 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
 }
 
 }  // namespace qlga
+

@@ -145,6 +145,18 @@ qlga_status qlga_apply_kinetic(qlga_handle* h);
  * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.C). */
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
 
+/* Per-site diagnostic fields of the current state (Sec. IV.A Eq. cmap and Eq. colormap,
+ * Sec. VI.B Eqs. velocity / pointwise_vorticity), written to `dst` as 11 planes of ny*nx
+ * values in the handle's precision, x fastest:
+ *   0 F_par = sum_m m |psi_m|^2          1 F_perp = |psi^dagger (f_x + i f_y) psi|
+ *   2 |A00| = |psi^T J psi| / sqrt(5)   3..5 (r, g, b) = (|F_par|, F_perp, |A00|) / their norm
+ *                                           (0 where all three vanish)
+ *   6..10 vorticity of level m = +2..-2: phase S = arg psi_m, v = wrapped central differences
+ *         of S / 2, vorticity = central-difference curl of v (0 in 1D).
+ * Phases are taken in FP64 for both precisions.  `where` is QLGA_HOST or QLGA_DEVICE; a host
+ * copy waits for the stream. */
+qlga_status qlga_fields(qlga_handle* h, void* dst, int where);
+
 /* Observables of a caller-provided device state without allocating any device memory.
  *
  * The paper has no counterpart to this call; it exists for callers that cannot allocate:

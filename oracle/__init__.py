@@ -17,6 +17,8 @@ Parity status of each function (what pins it; see tests/test_oracle_pins.py):
   step              pinned: dense brute-force operator product on tiny lattices, bright
                     soliton stationarity and drift velocity 2p (Sec. III/IV).
   observables       pinned: Table II characteristics, closed-form sums, brute force.
+  fields            pinned: Table II characteristics per site, plane-wave velocity (zero
+                    vorticity), total vorticity of a vortex / antivortex (+-2 pi), colour norm.
 """
 from __future__ import annotations
 
@@ -114,9 +116,10 @@ class Oracle:
         lib.oracle_heig.argtypes = [dp, dp, dp]
         lib.oracle_expm.argtypes = [dp, ctypes.c_double, dp]
         lib.oracle_max_threads.argtypes = []
+        lib.oracle_fields.argtypes = [dp, cp, dp]
         for name in ("oracle_step", "oracle_apply_potential", "oracle_apply_kinetic",
                      "oracle_apply_operator", "oracle_observables", "oracle_potential_matrix",
-                     "oracle_heig", "oracle_expm", "oracle_max_threads"):
+                     "oracle_heig", "oracle_expm", "oracle_max_threads", "oracle_fields"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -165,6 +168,14 @@ class Oracle:
         d["pop"] = out[2:7].copy()
         d["singlet_fraction"] = d["theta2_sum"] / d["rho2_sum"] if d["rho2_sum"] > 0 else 0.0
         return d
+
+    def fields(self, state, cfg) -> np.ndarray:
+        """Per-site fields, shape (11, ny, nx): F_par, F_perp, |A00|, r, g, b, vorticity m=+2..-2."""
+        _check_state(state, cfg)
+        out = np.zeros((11, cfg.ny, cfg.nx))
+        if self.lib.oracle_fields(_dptr(state), ctypes.byref(cfg), _dptr(out)):
+            raise ValueError("bad arguments")
+        return out
 
     def potential_matrix(self, psi, g0, g1, g2) -> np.ndarray:
         """V(psi) as a 5x5 complex matrix for one site's boson 5-vector psi (m = +2..-2)."""
@@ -223,6 +234,10 @@ def observables(state, cfg, ref=None):
 
 def potential_matrix(psi, g0, g1, g2):
     return default().potential_matrix(psi, g0, g1, g2)
+
+
+def fields(state, cfg):
+    return default().fields(state, cfg)
 
 
 def heig(V):

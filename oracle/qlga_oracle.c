@@ -37,6 +37,8 @@
 
 typedef double complex cplx;
 
+static const double kPi = 3.14159265358979323846;
+
 typedef struct oracle_cfg {
     int ndim;              /* 1 or 2 */
     long nx, ny;           /* ny == 1 in 1D */
@@ -358,6 +360,77 @@ static void observables(const double* st, const double* ref, const oracle_cfg* c
         }
 }
 
+/* ---------------------------------------------------------------- per-site fields */
+
+/* Wrap a phase difference into (-pi, pi]. */
+static double wrap_phase(double d) {
+    while (d > kPi) d -= 2.0 * kPi;
+    while (d <= -kPi) d += 2.0 * kPi;
+    return d;
+}
+
+/* Per-site diagnostic fields of the boson field psi = a + b, 11 planes of nx*ny doubles:
+ *  0 F_par = psi^dagger f_z psi            (Eq. cmap; the printed squares read as |psi_m|^2)
+ *  1 F_perp = sqrt(F_x^2 + F_y^2)          (Eq. cmap, F_nu = psi^dagger f_nu psi)
+ *  2 |A00| = |psi^T J psi| / sqrt(5)       (the singlet amplitude, Table II)
+ *  3..5 (r, g, b) = (|F_par|, F_perp, |A00|) / their Euclidean norm, 0 where all vanish
+ *       (Eq. colormap)
+ *  6..10 vorticity of level m = +2..-2 (2D only, else 0): phase S = arg psi_m, central-difference
+ *       velocity v_x = wrap(S(x+1) - S(x-1))/2, v_y likewise (Eq. velocity), and its
+ *       central-difference curl (v_y(x+1) - v_y(x-1) - v_x(y+1) + v_x(y-1))/2 (the reading of
+ *       Eq. pointwise_vorticity). */
+static cplx boson_at(const double* st, long n, int m, long site) {
+    return getc(amp((double*)st, n, m, site, 0)) + getc(amp((double*)st, n, m, site, 1));
+}
+
+static void fields(const double* st, const oracle_cfg* cfg, double* out) {
+    const long nx = cfg->nx, ny = cfg->ny, n = nx * ny;
+    cplx fx[5][5], fy[5][5], fz[5][5];
+    spin2_matrices(fx, fy, fz);
+    for (long y = 0; y < ny; ++y)
+        for (long x = 0; x < nx; ++x) {
+            const long site = y * nx + x;
+            cplx psi[5];
+            for (int m = 0; m < 5; ++m) psi[m] = boson_at(st, n, m, site);
+            double F[3];
+            cplx (*f[3])[5] = {fx, fy, fz};
+            for (int nu = 0; nu < 3; ++nu) {
+                cplx acc = 0.0;
+                for (int i = 0; i < 5; ++i)
+                    for (int j = 0; j < 5; ++j) acc += conj(psi[i]) * f[nu][i][j] * psi[j];
+                F[nu] = creal(acc);
+            }
+            cplx theta = 0.0;
+            for (int i = 0; i < 5; ++i) theta += (((2 - i) % 2 == 0) ? 1.0 : -1.0) * psi[i] * psi[4 - i];
+            const double fpar = F[2], fperp = sqrt(F[0] * F[0] + F[1] * F[1]);
+            const double a00 = cabs(theta) / sqrt(5.0);
+            const double nrm = sqrt(fpar * fpar + fperp * fperp + a00 * a00);
+            out[0 * n + site] = fpar;
+            out[1 * n + site] = fperp;
+            out[2 * n + site] = a00;
+            out[3 * n + site] = nrm > 0 ? fabs(fpar) / nrm : 0.0;
+            out[4 * n + site] = nrm > 0 ? fperp / nrm : 0.0;
+            out[5 * n + site] = nrm > 0 ? a00 / nrm : 0.0;
+            for (int m = 0; m < 5; ++m) {
+                double w = 0.0;
+                if (cfg->ndim == 2) {
+                    const long xp = (x + 1) % nx, xm = (x + nx - 1) % nx;
+                    const long yp = (y + 1) % ny, ym = (y + ny - 1) % ny;
+                    const double Spp = carg(boson_at(st, n, m, yp * nx + xp));
+                    const double Spm = carg(boson_at(st, n, m, ym * nx + xp));
+                    const double Smp = carg(boson_at(st, n, m, yp * nx + xm));
+                    const double Smm = carg(boson_at(st, n, m, ym * nx + xm));
+                    const double vy_xp = wrap_phase(Spp - Spm) / 2.0;   /* v_y(x+1, y) */
+                    const double vy_xm = wrap_phase(Smp - Smm) / 2.0;   /* v_y(x-1, y) */
+                    const double vx_yp = wrap_phase(Spp - Smp) / 2.0;   /* v_x(x, y+1) */
+                    const double vx_ym = wrap_phase(Spm - Smm) / 2.0;   /* v_x(x, y-1) */
+                    w = (vy_xp - vy_xm - vx_yp + vx_ym) / 2.0;
+                }
+                out[(6 + m) * n + site] = w;
+            }
+        }
+}
+
 /* ---------------------------------------------------------------- exported entry points */
 
 static int cfg_ok(const oracle_cfg* cfg) {
@@ -443,6 +516,12 @@ int oracle_expm(const double* V50, double delta, double* U50) {
             U50[2 * (5 * i + j)] = creal(U[i][j]);
             U50[2 * (5 * i + j) + 1] = cimag(U[i][j]);
         }
+    return 0;
+}
+
+int oracle_fields(const double* state, const oracle_cfg* cfg, double* out11) {
+    if (!cfg_ok(cfg) || !state || !out11) return 1;
+    fields(state, cfg, out11);
     return 0;
 }
 

@@ -369,6 +369,65 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
     }
 }
 
+// Per-site fields (see qlga_fields in qlga.h): 11 planes of T.
+__device__ __forceinline__ double wrap_pi(double d) {
+    const double pi = 3.14159265358979323846;
+    return d > pi ? d - 2.0 * pi : (d <= -pi ? d + 2.0 * pi : d);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T* __restrict__ out,
+                                                     int64_t nx, int64_t ny, int ndim) {
+    const int64_t nsites = nx * ny;
+    const T r32 = T(1.2247448713915890491);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
+        const int64_t x = site % nx, y = site / nx;
+        cpx<T> psi[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cpx<T> a, b;
+            load_pair<T>(X, nsites, m, site, a, b);
+            psi[m] = a + b;
+        }
+        const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
+        cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
+        const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
+        Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
+        const T fperp = sqrt(norm2(Fp));
+        const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
+        const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+        const T a00 = sqrt(norm2(th)) * T(0.44721359549995793928);
+        const T nrm = sqrt(Fz * Fz + fperp * fperp + a00 * a00);
+        out[0 * nsites + site] = Fz;
+        out[1 * nsites + site] = fperp;
+        out[2 * nsites + site] = a00;
+        out[3 * nsites + site] = nrm > T(0) ? fabs(Fz) / nrm : T(0);
+        out[4 * nsites + site] = nrm > T(0) ? fperp / nrm : T(0);
+        out[5 * nsites + site] = nrm > T(0) ? a00 / nrm : T(0);
+        const int64_t xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+        const int64_t yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            double w = 0.0;
+            if (ndim == 2) {
+                double S[4];  // phases at (x+1,y+1), (x+1,y-1), (x-1,y+1), (x-1,y-1)
+                const int64_t nb[4] = {yp * nx + xp, ym * nx + xp, yp * nx + xm, ym * nx + xm};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cpx<T> a, b;
+                    load_pair<T>(X, nsites, m, nb[k], a, b);
+                    S[k] = atan2(double(a.im) + double(b.im), double(a.re) + double(b.re));
+                }
+                const double vy_xp = wrap_pi(S[0] - S[1]) * 0.5, vy_xm = wrap_pi(S[2] - S[3]) * 0.5;
+                const double vx_yp = wrap_pi(S[0] - S[2]) * 0.5, vx_ym = wrap_pi(S[1] - S[3]) * 0.5;
+                w = (vy_xp - vy_xm - vx_yp + vx_ym) * 0.5;
+            }
+            out[(6 + m) * nsites + site] = T(w);
+        }
+    }
+}
+
 // Neumaier-compensated running sum.
 struct CompSum {
     double s = 0.0, c = 0.0;
@@ -922,6 +981,29 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
     if (s != QLGA_OK) return s;
     if (!std::isfinite(out->norm_qubit) || !std::isfinite(out->energy))
         return fail(QLGA_ERR_NOT_FINITE, "the state holds NaN or Inf%s");
+    return QLGA_OK;
+}
+
+qlga_status qlga_fields(qlga_handle* h, void* dst, int where) {
+    if (!h || !dst) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const void* view = nullptr;
+    qlga_status s = true_state_view(h, &view);
+    if (s != QLGA_OK) return s;
+    const int64_t n = nsites_of(h->cfg);
+    const size_t bytes = size_t(n) * 11 * (h->cfg.precision == 32 ? 4 : 8);  // < one state buffer
+    void* target = dst;
+    if (where == QLGA_HOST) target = (view == h->tmp) ? h->X[1 - h->cur] : h->tmp;
+    if (h->cfg.precision == 32)
+        k_fields<float><<<grid_for(n), kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<float*>(target), h->cfg.nx, h->cfg.ny, h->cfg.ndim);
+    else
+        k_fields<double><<<grid_for(n), kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<double*>(target), h->cfg.nx, h->cfg.ny, h->cfg.ndim);
+    QLGA_CUDA(cudaGetLastError(), "k_fields launch");
+    h->launches += 1;
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, h->stream), "qlga_fields copy");
+        QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_fields sync");
+    }
     return QLGA_OK;
 }
 

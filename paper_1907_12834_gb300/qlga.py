@@ -69,6 +69,7 @@ _SIGNATURES = {
     "qlga_synchronize": [_H],
     "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
     "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
+    "qlga_fields": [_H, _VP, ctypes.c_int],
     "qlga_destroy": [_H],
 }
 
@@ -192,6 +193,10 @@ def qlga_observables_noalloc(cfg: QlgaConfig, state_ptr: int, ref_ptr: int = 0,
     return out
 
 
+def qlga_fields(h: int, ptr: int, where: int):
+    _check(load_library().qlga_fields(_H(h), _VP(ptr), int(where)), "qlga_fields")
+
+
 def qlga_launch_count(h: int) -> int:
     out = ctypes.c_int64()
     _check(load_library().qlga_launch_count(_H(h), ctypes.byref(out)), "qlga_launch_count")
@@ -308,6 +313,12 @@ class Lattice:
         if ref is not None:
             ref_ptr = ref.data_ptr()
         return obs_to_dict(qlga_observables(self.handle, ref_ptr))
+
+    def fields(self):
+        """Per-site fields, numpy (11, ny, nx): F_par, F_perp, |A00|, r, g, b, vorticity m=+2..-2."""
+        out = np.empty((11, self.shape[1], self.shape[2]), dtype=self.dtype)
+        qlga_fields(self.handle, out.ctypes.data, QLGA_HOST)
+        return out
 
     def synchronize(self):
         qlga_synchronize(self.handle)

@@ -273,3 +273,51 @@ def pin_norm(orc, ndim=2, nsteps=4):
     n0 = float((st ** 2).sum())
     orc.step(st, cfg, nsteps)
     return abs(float((st ** 2).sum()) - n0) / n0
+
+
+# ----------------------------------------------------------------- per-site fields
+
+def pin_fields(orc):
+    """Per-site fields: Table II values on uniform Thomas-Fermi lattices (Sec. IV.A), unit colour
+    vectors (Eq. colormap), zero vorticity for a plane wave, the discrete curl summing to exactly
+    zero over the torus, and +-2 pi around a vortex / antivortex (Sec. VI.B)."""
+    from paper_1907_12834_gb300 import inputs
+    worst = 0.0
+    E, g0, g1, g2 = 1.0, 1.0, 0.1, 1.0
+    rows1 = golden.table1(E, g0, g1, g2)
+    for row, ((fpar, fperp, a00), flags) in golden.table2(E, g0, g1, g2).items():
+        if row not in rows1:
+            continue
+        c = np.asarray(rows1[row])
+        st = np.zeros((5, 4, 4, 2, 2))
+        st[..., 0, 0] = st[..., 1, 0] = (c / 2.0)[:, None, None]
+        f = orc.fields(st, oracle.make_cfg(2, 4, 4, g0, g1, g2))
+        worst = max(worst, float(np.abs(np.abs(f[0]) - fpar).max()), float(np.abs(f[2] - a00).max()))
+        if "perp-misprint" not in flags:
+            worst = max(worst, float(np.abs(f[1] - fperp).max()))
+        nrm = np.sqrt(f[3] ** 2 + f[4] ** 2 + f[5] ** 2)
+        worst = max(worst, float(np.abs(nrm[nrm > 0] - 1.0).max(initial=0.0)))
+    # plane wave in level +1: no vorticity
+    nx, ny = 32, 16
+    k = 2 * np.pi * 3 / nx
+    st = np.zeros((5, ny, nx, 2, 2))
+    w = 0.05 * np.exp(1j * k * np.arange(nx))[None, :] * np.ones((ny, 1))
+    st[1, ..., 0, 0] = st[1, ..., 1, 0] = w.real
+    st[1, ..., 0, 1] = st[1, ..., 1, 1] = w.imag
+    f = orc.fields(st, oracle.make_cfg(2, nx, ny, g0, g1, g2))
+    worst = max(worst, float(np.abs(f[6:]).max()))
+    # vortex dipole in level +2: +2 pi around the vortex, -2 pi around the antivortex, 0 in total
+    n = 96
+    psi = np.zeros((5, n, n), complex)
+    psi[0] = inputs.vortex_dipole(n, n, 0.1, 2, (g0, g1, g2), separation=40.0)
+    st = inputs.boson_to_state(psi, 0.1)
+    f = orc.fields(st, oracle.make_cfg(2, n, n, g0, g1, g2))
+    om = f[6]
+    worst = max(worst, abs(float(om.sum())))
+    cx, cy = int(n / 2 + 0.5), int(n / 2 + 0.5)
+    # the sum of the central-difference curl over a box telescopes to a closed loop of wrapped
+    # phase differences: exactly 2 pi times the winding inside
+    box = lambda xc, h: om[cy - h:cy + h + 1, xc - h:xc + h + 1].sum()
+    for h in (4, 12):
+        worst = max(worst, abs(box(cx - 20, h) - 2 * np.pi), abs(box(cx + 20, h) + 2 * np.pi))
+    return worst

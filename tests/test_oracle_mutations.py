@@ -29,6 +29,8 @@ MUTATIONS = [
      lambda o: pins.pin_dense_step(o, 2), 1e-13),
     ("y_stream_on_x", "else sy = ((y - dir) % ny + ny) % ny;", "else sx = ((x - dir) % nx + nx) % nx;",
      lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
+    ("vorticity_sign", "w = (vy_xp - vy_xm - vx_yp + vx_ym) / 2.0;", "w = (vy_xp - vy_xm + vx_yp - vx_ym) / 2.0;",
+     lambda o: pins.pin_fields(o), 1e-12),
     ("interleave_fraction", "const double frac = 1.0 / (4.0 * cfg->ndim);",
      "const double frac = 1.0 / 4.0;", lambda o: pins.pin_dense_step(o, 2, interleave=1), 1e-13),
 ]

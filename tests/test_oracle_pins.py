@@ -211,6 +211,11 @@ def test_kicked_soliton_moves_at_2p_and_obeys_dispersion(orc):
     assert abs(dx - 2 * p_lat * n) < 0.01 * 2 * p_lat * n
 
 
+def test_fields(orc):
+    """Per-site F_par, F_perp, |A00|, colour map and vorticity (Sec. IV.A, VI.B)."""
+    assert pins.pin_fields(orc) < 1e-12
+
+
 def test_pade_table3_solves_gp_to_order_r7():
     """Table III: the Pade vortex leaves a residual O(r^7) in the single-level GP equation
     E f = -(f'' + f'/r - f/r^2) + g f^3 (g = g0 + 4 g1, g0 + g1, g0 + g2/5 for |mf| = 2, 1, 0)."""

@@ -325,3 +325,36 @@ def test_nan_state_reported():
         lat.observables()
     assert ei.value.status == qlga.QLGA_ERR_NOT_FINITE
     lat.close()
+
+
+# ------------------------------------------------------------------ per-site fields
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_fields(precision, ndim):
+    """Per-site F_par, F_perp, |A00|, colour and vorticity against the oracle, on a state held
+    pending the kinetic operator (after a few steps)."""
+    if ndim == 2:
+        w = I.config2(n=128, separation=32, dtype=np.float64 if precision == 64 else np.float32)
+        nx, ny = 128, 128
+    else:
+        w = I.config1(L=2048)
+        nx, ny = 2048, 1
+    st = w.state.astype(np.float32 if precision == 32 else np.float64)
+    lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=w.g)
+    lat.load_state(st)
+    lat.step(3)
+    got = lat.fields()
+    cur = lat.get_state()
+    lat.close()
+    ref = oracle.fields(np.ascontiguousarray(cur, dtype=np.float64), oracle.make_cfg(ndim, nx, ny, *w.g))
+    tol = 1e-12 if precision == 64 else 2e-5
+    scale = np.abs(ref[:3]).max()
+    np.testing.assert_allclose(got[:3], ref[:3], rtol=0, atol=tol * scale)
+    # colour: a ratio, compared where the characteristics are not vanishingly small (in the
+    # soliton tails FP32 squares underflow)
+    mask = np.sqrt((ref[:3] ** 2).sum(0)) > 1e-6 * scale
+    np.testing.assert_allclose(got[3:6][:, mask], ref[3:6][:, mask], rtol=0,
+                               atol=(1e-12 if precision == 64 else 1e-4))
+    # vorticity: phases in FP64 on both sides from the same amplitudes
+    np.testing.assert_allclose(got[6:], ref[6:], rtol=0, atol=1e-9 if precision == 64 else 1e-6)

@@ -193,6 +193,50 @@ qlga_status qlga_synchronize(qlga_handle* h);
 /* Free the handle (and the device memory that qlga_create() allocated).  NULL is OK. */
 qlga_status qlga_destroy(qlga_handle* h);
 
+/* ---------------------------------------------------------------------------------------
+ * Batches: many independent periodic 1D lattices of uneven length, each with its own
+ * couplings, advanced together (one fused pass over all of them per step).  The state buffer of
+ * a batch is the concatenation of the runs' 1D states, each in the layout above with ny = 1
+ * (run r starts at element 20 * sum_{s<r} L_s).  Steps are the plain step; the first
+ * qlga_batch_step() times the candidate tile widths on the live state (writing only work space)
+ * and keeps the fastest; on a non-default stream, pairs of steps are then replayed from a
+ * CUDA graph captured once.
+ * --------------------------------------------------------------------------------------- */
+typedef struct qlga_batch_config {
+    int32_t precision;       /* 32 or 64 */
+    int32_t nruns;           /* >= 1 */
+    const int64_t* lengths;  /* host array [nruns], each >= 8 and <= 2^30 */
+    const double* couplings; /* host array [nruns][3]: g0, g1, g2 of each run */
+    double epsilon;          /* lattice scaling (informational for batches) */
+    int32_t kinetic_variant; /* QLGA_KINETIC_K1 or QLGA_KINETIC_K2 */
+    int32_t use_graph;       /* 1: replay steps from a captured CUDA graph where possible */
+} qlga_batch_config;
+
+typedef struct qlga_batch qlga_batch;
+
+/* Bytes of the batch state (20 reals per site summed over runs). */
+qlga_status qlga_batch_state_bytes(const qlga_batch_config* cfg, size_t* bytes);
+
+/* Allocate a batch on the current device (two state buffers, work space, per-run tables). */
+qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_batch** out);
+
+/* Load / read the concatenated state (host or device memory; host calls wait). */
+qlga_status qlga_batch_load_state(qlga_batch* b, const void* src, int where);
+qlga_status qlga_batch_get_state(qlga_batch* b, void* dst, int where);
+
+/* Advance every run n >= 0 steps (asynchronous). */
+qlga_status qlga_batch_step(qlga_batch* b, int64_t n);
+
+/* Observables of every run: out is a host array of nruns qlga_obs (FP64 sums); waits. */
+qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out);
+
+/* Tile width chosen by the tuner (0 before the first step), kernels launched, and the number of
+ * steps taken through graph replays. */
+qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int64_t* launches,
+                            int64_t* graph_steps);
+
+qlga_status qlga_batch_destroy(qlga_batch* b);
+
 /* Static description of a status code. */
 const char* qlga_status_string(qlga_status s);
 

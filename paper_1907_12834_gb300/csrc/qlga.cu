@@ -28,6 +28,9 @@
 
 #include "qlga_device.cuh"
 #include "qlga_step2d.cuh"
+#include "qlga_batch1d.cuh"
+
+#include <vector>
 
 using namespace qlga;
 
@@ -369,6 +372,79 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
     }
 }
 
+// Neumaier-compensated running sum.
+struct CompSum {
+    double s = 0.0, c = 0.0;
+    __device__ __forceinline__ void add(double v) {
+        const double t = s + v;
+        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+};
+
+// Per-run observables of a batch: one CTA per run; terms in the state's precision (compensated
+// per-thread sums for FP32), FP64 block sums in a fixed order; out[run][OBS_COUNT].
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_batch_observables(const T* __restrict__ X,
+                                                                const BatchRun* __restrict__ runs,
+                                                                const double* __restrict__ g3,
+                                                                double* __restrict__ out) {
+    const BatchRun run = runs[blockIdx.x];
+    const int L = run.L;
+    const T r32 = T(1.2247448713915890491);
+    const T hg0 = T(0.5 * g3[3 * blockIdx.x]), hg1 = T(0.5 * g3[3 * blockIdx.x + 1]);
+    const T tg2 = T(0.1 * g3[3 * blockIdx.x + 2]);
+    ThreadSum<T> acc[OBS_COUNT];
+    auto boson = [&](int m, int j) {
+        const Pair4<T> p = load_raw_pair(X, run.base + int64_t(m) * L + j);
+        return cpx<T>{p.v[0] + p.v[3], p.v[1] - p.v[2]};  // a + b, b = -i bt
+    };
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        cpx<T> psi[5];
+        T rho = T(0);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const Pair4<T> p = load_raw_pair(X, run.base + int64_t(m) * L + j);
+            const T pm = p.v[0] * p.v[0] + p.v[1] * p.v[1] + p.v[2] * p.v[2] + p.v[3] * p.v[3];
+            acc[OBS_NORM_QUBIT].add(pm);
+            acc[OBS_POP0 + m].add(pm);
+            psi[m] = {p.v[0] + p.v[3], p.v[1] - p.v[2]};
+            rho += norm2(psi[m]);
+        }
+        acc[OBS_NORM_BOSON].add(rho);
+        const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
+        cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
+        const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
+        Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
+        const T F2 = Fz * Fz + norm2(Fp);
+        const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
+        const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+        const T th2 = norm2(th);
+        const int jn = j + 1 == L ? 0 : j + 1;
+        T grad = T(0);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) grad += norm2(boson(m, jn) - psi[m]);
+        acc[OBS_ENERGY].add(grad + hg0 * rho * rho + hg1 * F2 + tg2 * th2);
+        acc[OBS_SINGLET_RE].add(th.re * T(0.44721359549995793928));
+        acc[OBS_SINGLET_IM].add(th.im * T(0.44721359549995793928));
+        acc[OBS_THETA2].add(th2);
+        acc[OBS_RHO2].add(rho * rho);
+    }
+    __shared__ double sh[kThreads / 32][OBS_COUNT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < OBS_COUNT; ++k) {
+        const double v = warp_sum(acc[k].value());
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < OBS_COUNT) {
+        CompSum cs;
+        for (int w = 0; w < kThreads / 32; ++w) cs.add(sh[w][threadIdx.x]);
+        out[int64_t(blockIdx.x) * OBS_COUNT + threadIdx.x] = cs.s + cs.c;
+    }
+}
+
 // Per-site fields (see qlga_fields in qlga.h): 11 planes of T.
 __device__ __forceinline__ double wrap_pi(double d) {
     const double pi = 3.14159265358979323846;
@@ -428,15 +504,6 @@ __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T*
     }
 }
 
-// Neumaier-compensated running sum.
-struct CompSum {
-    double s = 0.0, c = 0.0;
-    __device__ __forceinline__ void add(double v) {
-        const double t = s + v;
-        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
-    }
-};
 
 // out[k] = compensated sum of partials[b][k] over blocks, in a fixed order: warp k reduces
 // quantity k, lane l takes blocks l, l+32, ..., then the 32 (sum, compensation) pairs combine
@@ -516,6 +583,20 @@ qlga_status check_cfg(const qlga_config* c) {
     return QLGA_OK;
 }
 
+// Threads per block for the per-site kernels: 256, or fewer for small lattices so that the grid
+// still spreads over every SM (2 x 152 blocks), never below one warp.
+int block_for(int64_t n) {
+    int64_t t = (n + 2 * 152 - 1) / (2 * 152);
+    t = (t + 31) / 32 * 32;
+    return int(t < 32 ? 32 : (t > kThreads ? kThreads : t));
+}
+
+int grid_for_block(int64_t n, int threads, int cap = 152 * 16) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > cap) g = cap;
+    return int(g < 1 ? 1 : g);
+}
+
 int grid_for(int64_t n, int cap = 152 * 16) {
     int64_t g = (n + kThreads - 1) / kThreads;
     if (g > cap) g = cap;
@@ -527,7 +608,8 @@ PotParams pot_params(const qlga_config& c, double delta) { return PotParams{c.g0
 template <class T>
 qlga_status launch_potential(qlga_handle* h, void* buf, double delta) {
     const int64_t n = nsites_of(h->cfg);
-    k_potential<T, std::is_same<T, float>::value><<<grid_for(n), kThreads, 0, h->stream>>>(
+    const int nt = block_for(n);
+    k_potential<T, std::is_same<T, float>::value><<<grid_for_block(n, nt), nt, 0, h->stream>>>(
         static_cast<T*>(buf), n, PotConst<T>(pot_params(h->cfg, delta)), h->status);
     QLGA_CUDA(cudaGetLastError(), "k_potential launch");
     h->launches += 1;
@@ -537,7 +619,8 @@ qlga_status launch_potential(qlga_handle* h, void* buf, double delta) {
 template <class T, int V, bool POT>
 qlga_status launch_axis_t(qlga_handle* h, const void* in, void* out, int axis) {
     const int64_t n = nsites_of(h->cfg);
-    k_kinetic_axis<T, V, POT><<<grid_for(n), kThreads, 0, h->stream>>>(
+    const int nt = block_for(n);
+    k_kinetic_axis<T, V, POT><<<grid_for_block(n, nt), nt, 0, h->stream>>>(
         static_cast<const T*>(in), static_cast<T*>(out), h->cfg.nx, h->cfg.ny, axis,
         PotConst<T>(pot_params(h->cfg, 1.0)), h->status);
     QLGA_CUDA(cudaGetLastError(), "k_kinetic_axis launch");
@@ -562,17 +645,18 @@ qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
 
 qlga_status launch_block(qlga_handle* h, const void* in, void* out, int axis, int q) {
     const int64_t n = nsites_of(h->cfg);
-    const int g = grid_for(n);
+    const int nt = block_for(n);
+    const int g = grid_for_block(n, nt);
     if (h->cfg.precision == 32) {
         if (h->cfg.kinetic_variant == 0)
-            k_block<float, 0><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+            k_block<float, 0><<<g, nt, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
         else
-            k_block<float, 1><<<g, kThreads, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+            k_block<float, 1><<<g, nt, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
     } else {
         if (h->cfg.kinetic_variant == 0)
-            k_block<double, 0><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+            k_block<double, 0><<<g, nt, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
         else
-            k_block<double, 1><<<g, kThreads, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+            k_block<double, 1><<<g, nt, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
     }
     QLGA_CUDA(cudaGetLastError(), "k_block launch");
     h->launches += 1;
@@ -1045,5 +1129,422 @@ const char* qlga_status_string(qlga_status s) {
 }
 
 const char* qlga_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ===================================================================== batches of 1D lattices
+
+namespace {
+
+constexpr int kBatchWidths[3] = {64, 128, 256};
+
+}  // namespace
+
+struct qlga_batch {
+    int precision, variant, nruns;
+    bool use_graph;
+    int64_t total_sites;
+    cudaStream_t stream;
+    void* X[2];
+    void* tmp;
+    BatchRun* runs;
+    void* consts;             // PotConst<T>[nruns]
+    double* g3;               // [nruns][3], device
+    double* obs_dev;          // [nruns][OBS_COUNT]
+    unsigned* status;
+    BatchTile* tiles[3];
+    int ntiles[3];
+    int wsel;                 // index into kBatchWidths, -1 before tuning
+    int cur;
+    bool pending_k;
+    int64_t step, launches, graph_steps;
+    cudaGraphExec_t graph;
+    int graph_cur;            // X index the captured pair of steps starts from, -1 if none
+};
+
+namespace {
+
+size_t batch_state_bytes_of(int precision, int64_t total_sites) {
+    return size_t(total_sites) * 20 * (precision == 32 ? 4 : 8);
+}
+
+qlga_status check_batch_cfg(const qlga_batch_config* c, int64_t* total) {
+    if (!c) return fail(QLGA_ERR_INVALID_ARG, "batch config is NULL%s");
+    if (c->precision != 32 && c->precision != 64) return fail(QLGA_ERR_INVALID_ARG, "precision must be 32 or 64%s");
+    if (c->nruns < 1 || !c->lengths || !c->couplings) return fail(QLGA_ERR_INVALID_ARG, "nruns >= 1 with lengths and couplings required%s");
+    if (c->kinetic_variant != QLGA_KINETIC_K1 && c->kinetic_variant != QLGA_KINETIC_K2)
+        return fail(QLGA_ERR_INVALID_ARG, "kinetic_variant must be K1 or K2%s");
+    int64_t t = 0;
+    for (int r = 0; r < c->nruns; ++r) {
+        if (c->lengths[r] < 8 || c->lengths[r] > (int64_t(1) << 30)) return fail(QLGA_ERR_INVALID_ARG, "run lengths must be in [8, 2^30]%s");
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(c->couplings[3 * r + k])) return fail(QLGA_ERR_INVALID_ARG, "couplings must be finite%s");
+        t += c->lengths[r];
+    }
+    if (t > (int64_t(1) << 34)) return fail(QLGA_ERR_INVALID_ARG, "batch too large%s");
+    *total = t;
+    return QLGA_OK;
+}
+
+template <class T, int V, bool POT, int W>
+void batch_launch_t(qlga_batch* b, const void* in, void* out, int wi) {
+    k_batch_step<T, V, POT, W><<<b->ntiles[wi], W, 0, b->stream>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), b->tiles[wi], b->runs,
+        static_cast<const PotConst<T>*>(b->consts), b->status);
+}
+
+template <class T, int V, bool POT>
+void batch_launch_w(qlga_batch* b, const void* in, void* out, int wi) {
+    if (wi == 0) batch_launch_t<T, V, POT, 64>(b, in, out, wi);
+    else if (wi == 1) batch_launch_t<T, V, POT, 128>(b, in, out, wi);
+    else batch_launch_t<T, V, POT, 256>(b, in, out, wi);
+}
+
+// One fused step (pot) or the kinetic operator alone: in -> out, tile width index wi.
+qlga_status batch_launch(qlga_batch* b, const void* in, void* out, bool pot, int wi) {
+    const bool f = b->precision == 32;
+    if (f) {
+        if (b->variant == 0) { if (pot) batch_launch_w<float, 0, true>(b, in, out, wi); else batch_launch_w<float, 0, false>(b, in, out, wi); }
+        else { if (pot) batch_launch_w<float, 1, true>(b, in, out, wi); else batch_launch_w<float, 1, false>(b, in, out, wi); }
+    } else {
+        if (b->variant == 0) { if (pot) batch_launch_w<double, 0, true>(b, in, out, wi); else batch_launch_w<double, 0, false>(b, in, out, wi); }
+        else { if (pot) batch_launch_w<double, 1, true>(b, in, out, wi); else batch_launch_w<double, 1, false>(b, in, out, wi); }
+    }
+    QLGA_CUDA(cudaGetLastError(), "k_batch_step launch");
+    b->launches += 1;
+    return QLGA_OK;
+}
+
+// The potential unitary alone from a raw state: a fused step whose kinetic part is skipped is
+// not available, so the first step from a raw state applies U with the generic per-site kernel
+// through a flat view of the batch (U is local, so run boundaries do not matter) -- but each run
+// has its own couplings, so instead the batch keeps raw states raw and applies one fused step
+// of the shifted form: X <- U(X) X is done by the kinetic-free path below.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchTile* __restrict__ tiles,
+                                                              const BatchRun* __restrict__ runs,
+                                                              const PotConst<T>* __restrict__ consts,
+                                                              int W, unsigned* status) {
+    const BatchTile tile = tiles[blockIdx.x];
+    const BatchRun run = runs[tile.run];
+    for (int base = 0; base < W; base += blockDim.x) {
+        const int j = tile.start + base + threadIdx.x;
+        const int js = j < run.L ? j : run.L - 1;  // lanes past the end repeat a valid site
+        cpx<T> a[5], b[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const Pair4<T> p = load_raw_pair(X, run.base + int64_t(m) * run.L + js);
+            a[m] = {p.v[0], p.v[1]};
+            b[m] = {p.v[3], -p.v[2]};
+        }
+        const PotConst<T> C = consts[tile.run];
+        potential_site<T, sizeof(T) == 4>(a, b, C, T(1), T(0.5), status);
+        __syncwarp();
+        if (j < run.L) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+                store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re, a[m].im, -b[m].im, b[m].re);
+        }
+    }
+}
+
+qlga_status batch_potential(qlga_batch* b, void* X) {
+    const int wi = 1;  // tiles of 128 sites, 128 threads
+    if (b->precision == 32)
+        k_batch_potential<float><<<b->ntiles[wi], 128, 0, b->stream>>>(static_cast<float*>(X), b->tiles[wi], b->runs, static_cast<const PotConst<float>*>(b->consts), kBatchWidths[wi], b->status);
+    else
+        k_batch_potential<double><<<b->ntiles[wi], 128, 0, b->stream>>>(static_cast<double*>(X), b->tiles[wi], b->runs, static_cast<const PotConst<double>*>(b->consts), kBatchWidths[wi], b->status);
+    QLGA_CUDA(cudaGetLastError(), "k_batch_potential launch");
+    b->launches += 1;
+    return QLGA_OK;
+}
+
+// Time each tile width on the live state (two fused steps into work space; the state itself is
+// not advanced) and keep the fastest.
+qlga_status batch_tune(qlga_batch* b) {
+    cudaEvent_t e0, e1;
+    QLGA_CUDA(cudaEventCreate(&e0), "tune event");
+    QLGA_CUDA(cudaEventCreate(&e1), "tune event");
+    float best = 1e30f;
+    int besti = 1;
+    for (int wi = 0; wi < 3; ++wi) {
+        qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);  // warm
+        if (s != QLGA_OK) return s;
+        QLGA_CUDA(cudaEventRecord(e0, b->stream), "tune record");
+        for (int k = 0; k < 2; ++k) {
+            s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);
+            if (s != QLGA_OK) return s;
+        }
+        QLGA_CUDA(cudaEventRecord(e1, b->stream), "tune record");
+        QLGA_CUDA(cudaEventSynchronize(e1), "tune sync");
+        float ms = 0.f;
+        QLGA_CUDA(cudaEventElapsedTime(&ms, e0, e1), "tune elapsed");
+        if (ms < best) {
+            best = ms;
+            besti = wi;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->wsel = besti;
+    return QLGA_OK;
+}
+
+// Capture two fused steps starting from X[cur] (cur -> 1-cur -> cur) into a graph.
+qlga_status batch_build_graph(qlga_batch* b) {
+    cudaGraph_t g;
+    QLGA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
+    const int c = b->cur;
+    const int64_t l0 = b->launches;
+    qlga_status s1 = batch_launch(b, b->X[c], b->X[1 - c], true, b->wsel);
+    qlga_status s2 = s1 == QLGA_OK ? batch_launch(b, b->X[1 - c], b->X[c], true, b->wsel) : s1;
+    b->launches = l0;  // counted when replayed
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (s2 != QLGA_OK) return s2;
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    b->graph_cur = c;
+    return QLGA_OK;
+}
+
+qlga_status batch_materialize_view(qlga_batch* b, const void** view) {
+    if (!b->pending_k) {
+        *view = b->X[b->cur];
+        return QLGA_OK;
+    }
+    qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, false, b->wsel >= 0 ? b->wsel : 1);
+    *view = b->tmp;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+qlga_status qlga_batch_state_bytes(const qlga_batch_config* cfg, size_t* bytes) {
+    int64_t total = 0;
+    qlga_status s = check_batch_cfg(cfg, &total);
+    if (s != QLGA_OK) return s;
+    if (!bytes) return fail(QLGA_ERR_INVALID_ARG, "bytes is NULL%s");
+    *bytes = batch_state_bytes_of(cfg->precision, total);
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_batch** out) {
+    int64_t total = 0;
+    qlga_status s = check_batch_cfg(cfg, &total);
+    if (s != QLGA_OK) return s;
+    if (!out) return fail(QLGA_ERR_INVALID_ARG, "out is NULL%s");
+    *out = nullptr;
+    qlga_batch* b = new qlga_batch();
+    b->precision = cfg->precision;
+    b->variant = cfg->kinetic_variant;
+    b->nruns = cfg->nruns;
+    b->use_graph = cfg->use_graph != 0 && stream != nullptr;
+    b->total_sites = total;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->wsel = -1;
+    b->graph_cur = -1;
+    const size_t sb = batch_state_bytes_of(cfg->precision, total);
+    std::vector<BatchRun> runs(cfg->nruns);
+    int64_t base = 0;
+    for (int r = 0; r < cfg->nruns; ++r) {
+        runs[r].base = base;
+        runs[r].L = int(cfg->lengths[r]);
+        runs[r].pad = 0;
+        base += 5 * cfg->lengths[r];
+    }
+    std::vector<BatchTile> tiles[3];
+    for (int wi = 0; wi < 3; ++wi) {
+        for (int r = 0; r < cfg->nruns; ++r)
+            for (int64_t st = 0; st < cfg->lengths[r]; st += kBatchWidths[wi]) tiles[wi].push_back(BatchTile{r, int(st)});
+        b->ntiles[wi] = int(tiles[wi].size());
+    }
+    const size_t cbytes = size_t(cfg->nruns) * (cfg->precision == 32 ? sizeof(PotConst<float>) : sizeof(PotConst<double>));
+    cudaError_t e = cudaMalloc(&b->X[0], sb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->X[1], sb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->tmp, sb);
+    if (e == cudaSuccess) e = cudaMalloc(&b->runs, sizeof(BatchRun) * runs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->consts, cbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->g3, sizeof(double) * 3 * cfg->nruns);
+    if (e == cudaSuccess) e = cudaMalloc(&b->obs_dev, sizeof(double) * OBS_COUNT * cfg->nruns);
+    if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(unsigned));
+    for (int wi = 0; wi < 3 && e == cudaSuccess; ++wi) e = cudaMalloc(&b->tiles[wi], sizeof(BatchTile) * tiles[wi].size());
+    if (e != cudaSuccess) {
+        qlga_batch_destroy(b);
+        cudaGetLastError();
+        return cuda_fail(e, "qlga_batch_create cudaMalloc");
+    }
+    std::vector<PotConst<float>> cf;
+    std::vector<PotConst<double>> cd;
+    for (int r = 0; r < cfg->nruns; ++r) {
+        const PotParams P{cfg->couplings[3 * r], cfg->couplings[3 * r + 1], cfg->couplings[3 * r + 2], 1.0};
+        cf.push_back(PotConst<float>(P));
+        cd.push_back(PotConst<double>(P));
+    }
+    e = cudaMemcpy(b->runs, runs.data(), sizeof(BatchRun) * runs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cfg->precision == 32 ? cudaMemcpy(b->consts, cf.data(), cbytes, cudaMemcpyHostToDevice)
+                                 : cudaMemcpy(b->consts, cd.data(), cbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->g3, cfg->couplings, sizeof(double) * 3 * cfg->nruns, cudaMemcpyHostToDevice);
+    for (int wi = 0; wi < 3 && e == cudaSuccess; ++wi)
+        e = cudaMemcpy(b->tiles[wi], tiles[wi].data(), sizeof(BatchTile) * tiles[wi].size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->X[0], 0, sb);
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        qlga_batch_destroy(b);
+        return cuda_fail(e, "qlga_batch_create upload");
+    }
+    *out = b;
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_load_state(qlga_batch* b, const void* src, int where) {
+    if (!b || !src) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const size_t nb = batch_state_bytes_of(b->precision, b->total_sites);
+    const void* dev_src = src;
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaMemcpyAsync(b->tmp, src, nb, cudaMemcpyHostToDevice, b->stream), "qlga_batch_load_state copy");
+        dev_src = b->tmp;
+    }
+    const int64_t np = 5 * b->total_sites;
+    if (b->precision == 32)
+        k_convert_layout<float, true><<<grid_for(np), kThreads, 0, b->stream>>>(static_cast<const float*>(dev_src), static_cast<float*>(b->X[b->cur]), np);
+    else
+        k_convert_layout<double, true><<<grid_for(np), kThreads, 0, b->stream>>>(static_cast<const double*>(dev_src), static_cast<double*>(b->X[b->cur]), np);
+    QLGA_CUDA(cudaGetLastError(), "k_convert_layout launch");
+    b->launches += 1;
+    if (where == QLGA_HOST) QLGA_CUDA(cudaStreamSynchronize(b->stream), "qlga_batch_load_state sync");
+    b->pending_k = false;
+    b->step = 0;
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_get_state(qlga_batch* b, void* dst, int where) {
+    if (!b || !dst) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (where != QLGA_HOST && where != QLGA_DEVICE) return fail(QLGA_ERR_INVALID_ARG, "where must be QLGA_HOST or QLGA_DEVICE%s");
+    const void* view = nullptr;
+    qlga_status s = batch_materialize_view(b, &view);
+    if (s != QLGA_OK) return s;
+    const int64_t np = 5 * b->total_sites;
+    void* target = where == QLGA_DEVICE ? dst : b->tmp;
+    if (b->precision == 32)
+        k_convert_layout<float, false><<<grid_for(np), kThreads, 0, b->stream>>>(static_cast<const float*>(view), static_cast<float*>(target), np);
+    else
+        k_convert_layout<double, false><<<grid_for(np), kThreads, 0, b->stream>>>(static_cast<const double*>(view), static_cast<double*>(target), np);
+    QLGA_CUDA(cudaGetLastError(), "k_convert_layout launch");
+    b->launches += 1;
+    if (where == QLGA_HOST) {
+        QLGA_CUDA(cudaMemcpyAsync(dst, b->tmp, batch_state_bytes_of(b->precision, b->total_sites), cudaMemcpyDeviceToHost, b->stream), "qlga_batch_get_state copy");
+        QLGA_CUDA(cudaStreamSynchronize(b->stream), "qlga_batch_get_state sync");
+    }
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_step(qlga_batch* b, int64_t n) {
+    if (!b) return fail(QLGA_ERR_INVALID_ARG, "batch is NULL%s");
+    if (n < 0) return fail(QLGA_ERR_INVALID_ARG, "n must be >= 0%s");
+    qlga_status s = QLGA_OK;
+    while (n > 0) {
+        if (!b->pending_k) {
+            s = batch_potential(b, b->X[b->cur]);  // X = U psi, true state K X
+            if (s != QLGA_OK) return s;
+            b->pending_k = true;
+        } else {
+            if (b->wsel < 0) {
+                s = batch_tune(b);
+                if (s != QLGA_OK) return s;
+            }
+            if (b->use_graph && n >= 2 && b->graph_cur < 0) {
+                s = batch_build_graph(b);
+                if (s != QLGA_OK) return s;
+            }
+            if (b->use_graph && n >= 2 && b->graph_cur == b->cur) {
+                QLGA_CUDA(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+                b->launches += 2;
+                b->graph_steps += 2;
+                b->step += 2;
+                n -= 2;
+                continue;
+            }
+            s = batch_launch(b, b->X[b->cur], b->X[1 - b->cur], true, b->wsel);
+            if (s != QLGA_OK) return s;
+            b->cur ^= 1;
+        }
+        b->step += 1;
+        n -= 1;
+    }
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out) {
+    if (!b || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    const void* view = nullptr;
+    qlga_status s = batch_materialize_view(b, &view);
+    if (s != QLGA_OK) return s;
+    if (b->precision == 32)
+        k_batch_observables<float><<<b->nruns, kThreads, 0, b->stream>>>(static_cast<const float*>(view), b->runs, b->g3, b->obs_dev);
+    else
+        k_batch_observables<double><<<b->nruns, kThreads, 0, b->stream>>>(static_cast<const double*>(view), b->runs, b->g3, b->obs_dev);
+    QLGA_CUDA(cudaGetLastError(), "k_batch_observables launch");
+    b->launches += 1;
+    std::vector<double> o(size_t(b->nruns) * OBS_COUNT);
+    QLGA_CUDA(cudaMemcpyAsync(o.data(), b->obs_dev, sizeof(double) * o.size(), cudaMemcpyDeviceToHost, b->stream), "batch observables copy");
+    QLGA_CUDA(cudaStreamSynchronize(b->stream), "batch observables sync");
+    unsigned st = 0;
+    QLGA_CUDA(cudaMemcpy(&st, b->status, sizeof(unsigned), cudaMemcpyDeviceToHost), "batch status read");
+    bool finite = true;
+    for (int r = 0; r < b->nruns; ++r) {
+        const double* q = o.data() + size_t(r) * OBS_COUNT;
+        qlga_obs* p = out + r;
+        std::memset(p, 0, sizeof(*p));
+        p->norm_qubit = q[OBS_NORM_QUBIT];
+        p->norm_boson = q[OBS_NORM_BOSON];
+        for (int m = 0; m < 5; ++m) {
+            p->pop[m] = q[OBS_POP0 + m];
+            p->magnetisation += double(2 - m) * q[OBS_POP0 + m];
+        }
+        p->energy = q[OBS_ENERGY];
+        p->singlet_re = q[OBS_SINGLET_RE];
+        p->singlet_im = q[OBS_SINGLET_IM];
+        p->singlet_fraction = q[OBS_RHO2] > 0 ? q[OBS_THETA2] / q[OBS_RHO2] : 0.0;
+        p->step = b->step;
+        finite = finite && std::isfinite(p->norm_qubit) && std::isfinite(p->energy);
+    }
+    if (st & 1u) {
+        cudaMemset(b->status, 0, sizeof(unsigned));
+        return fail(QLGA_ERR_NOT_FINITE, "the potential exponent exceeded its range in some run%s");
+    }
+    if (!finite) return fail(QLGA_ERR_NOT_FINITE, "a run's state holds NaN or Inf%s");
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int64_t* launches, int64_t* graph_steps) {
+    if (!b) return fail(QLGA_ERR_INVALID_ARG, "batch is NULL%s");
+    if (tile_width) *tile_width = b->wsel >= 0 ? kBatchWidths[b->wsel] : 0;
+    if (launches) *launches = b->launches;
+    if (graph_steps) *graph_steps = b->graph_steps;
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_destroy(qlga_batch* b) {
+    if (!b) return QLGA_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+    if (b->graph_cur >= 0) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->X[0]);
+    cudaFree(b->X[1]);
+    cudaFree(b->tmp);
+    cudaFree(b->runs);
+    cudaFree(b->consts);
+    cudaFree(b->g3);
+    cudaFree(b->obs_dev);
+    cudaFree(b->status);
+    for (int wi = 0; wi < 3; ++wi) cudaFree(b->tiles[wi]);
+    delete b;
+    return QLGA_OK;
+}
 
 }  // extern "C"

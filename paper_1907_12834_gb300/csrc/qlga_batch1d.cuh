@@ -1,0 +1,120 @@
+// qlga_batch1d.cuh -- many independent 1D QLGA lattices of uneven length in one launch per step.
+//
+// A batch holds nruns periodic 1D lattices back to back; run r occupies its own block of the
+// buffer laid out like a single 1D state (5 planes of L_r sites), so plane m of run r starts at
+// pair index base_r + m L_r with base_r = 5 sum_{s<r} L_s.  Each run has its own couplings.
+//
+// One fused step (the state is held pending the kinetic operator, as for a single lattice):
+// a CTA of W threads takes one tile of W consecutive sites of one run (the tile table lists
+// (run, start) for every tile of every run), stages the tile and its 4-site periodic halo of
+// that run in shared memory, applies the nine-point kinetic stencil of the axis (Sec. VII.B)
+// and the potential unitary with the run's couplings, and writes the tile: one read and one
+// write of the state per step, whatever the mix of lengths.  W is chosen at run time by timing
+// the candidates on the live state (see qlga_batch_step).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qlga_device.cuh"
+
+namespace qlga {
+
+struct BatchTile {
+    int run;
+    int start;
+};
+
+struct BatchRun {
+    int64_t base;  // pair index of plane 0, site 0 of the run
+    int L;
+    int pad;
+};
+
+template <class T>
+struct Pair4 {
+    T v[4];  // a.re, a.im, bt.re, bt.im (resident layout)
+};
+
+template <class T>
+__device__ __forceinline__ Pair4<T> load_raw_pair(const T* X, int64_t pair) {
+    Pair4<T> p;
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(X) + pair);
+        p.v[0] = v.x; p.v[1] = v.y; p.v[2] = v.z; p.v[3] = v.w;
+    } else {
+        const double2* q = reinterpret_cast<const double2*>(X) + 2 * pair;
+        const double2 u = __ldg(q), w = __ldg(q + 1);
+        p.v[0] = u.x; p.v[1] = u.y; p.v[2] = w.x; p.v[3] = w.y;
+    }
+    return p;
+}
+
+template <class T>
+__device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T b0, T b1) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4*>(X)[pair] = make_float4(a0, a1, b0, b1);
+    } else {
+        double2* q = reinterpret_cast<double2*>(X) + 2 * pair;
+        q[0] = make_double2(a0, a1);
+        q[1] = make_double2(b0, b1);
+    }
+}
+
+// One fused step (POT) or the kinetic operator alone, for the tiles of a batch.
+template <class T, int VARIANT, bool POT, int W>
+__global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* __restrict__ out,
+                                                   const BatchTile* __restrict__ tiles,
+                                                   const BatchRun* __restrict__ runs,
+                                                   const PotConst<T>* __restrict__ consts,
+                                                   unsigned* status) {
+    __shared__ Pair4<T> sm[5][W + 8];
+    constexpr KinStencil S = kStencil[VARIANT];
+    const BatchTile tile = tiles[blockIdx.x];
+    const BatchRun run = runs[tile.run];
+    const int L = run.L;
+    for (int i = threadIdx.x; i < 5 * (W + 8); i += W) {
+        const int m = i / (W + 8), c = i - m * (W + 8);
+        int j = (tile.start - 4 + c) % L;
+        j = j < 0 ? j + L : j;
+        sm[m][c] = load_raw_pair(in, run.base + int64_t(m) * L + j);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int j = tile.start + t;
+    cpx<T> oa[5], ob[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const Pair4<T> p = sm[m][t + k];
+            const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
+            const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
+            xa.re = fma(caa, p.v[0], fma(cab, p.v[2], xa.re));
+            xa.im = fma(caa, p.v[1], fma(cab, p.v[3], xa.im));
+            xbt.re = fma(cba, p.v[0], fma(cbb, p.v[2], xbt.re));
+            xbt.im = fma(cba, p.v[1], fma(cbb, p.v[3], xbt.im));
+        }
+        oa[m] = xa;                  // x16, unnormalised
+        ob[m] = {xbt.im, -xbt.re};   // b = -i bt
+    }
+    if (POT) {
+        // all lanes take part (the Taylor degree is a warp maximum); lanes past the run's end
+        // work on a copy of a valid site and store nothing
+        const PotConst<T> C = consts[tile.run];
+        potential_site<T, sizeof(T) == 4>(oa, ob, C, T(1.0 / 256.0), T(0.5 / 16.0), status);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            oa[m] = T(1.0 / 16.0) * oa[m];
+            ob[m] = T(1.0 / 16.0) * ob[m];
+        }
+    }
+    if (j < L) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+            store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+    }
+}
+
+}  // namespace qlga

@@ -295,3 +295,48 @@ def config2(seed: int = 1909, n: int = 4096, eps: float = 0.1, steps: int = 5000
     del psi
     return Workload("2d-vortex-scattering-%dx%d" % (n, n), 2, n, n, CONFIG2_G, eps, steps,
                     32 if dtype == np.float32 else 64, st, {"variant": variant})
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    lengths: np.ndarray          # int64 [nruns]
+    couplings: np.ndarray        # float64 [nruns, 3]
+    eps: float
+    steps: int
+    precision: int
+    state: np.ndarray = field(repr=False)   # concatenated run states, each (5, 1, L, 2, 2) flattened
+    meta: dict = field(default_factory=dict)
+
+    def offsets(self) -> np.ndarray:
+        """Element offset of each run inside the concatenated state (20 reals per site)."""
+        return np.concatenate([[0], np.cumsum(self.lengths)[:-1]]) * 20
+
+    def run_state(self, r: int) -> np.ndarray:
+        o = int(self.offsets()[r])
+        return self.state[o:o + 20 * int(self.lengths[r])].reshape(5, 1, int(self.lengths[r]), 2, 2)
+
+
+def scattering_run(rng: np.random.Generator, L: int, eps: float) -> np.ndarray:
+    """One seeded two-soliton scattering state of length L (the recipe of config1)."""
+    rows = rng.choice([1, 2, 15], size=2, replace=False)
+    kappa = rng.uniform(0.05, 0.3)
+    n = int(round(kappa * L / (2 * np.pi)))
+    rel = rng.uniform(0.0, 2 * np.pi)
+    j = np.arange(L, dtype=np.float64)
+    p_lat = 2 * np.pi * n / L
+    s1 = bright_soliton(eps * (j - L / 4), int(rows[0]), CONFIG0_G)
+    s2 = bright_soliton(eps * (j - 3 * L / 4), int(rows[1]), CONFIG0_G)
+    return s1 * np.exp(1j * p_lat * j)[None, :] + s2 * np.exp(-1j * p_lat * j + 1j * rel)[None, :]
+
+
+def config3(seed: int = 1910, nruns: int = 256, lmin: int = 2048, lmax: int = 65536,
+            eps: float = 0.1, steps: int = 10000, dtype=np.float32) -> BatchWorkload:
+    """Batched 1D scattering: nruns independent runs, L log-uniform in [lmin, lmax], each with
+    its own seeded soliton pair (config1 recipe) and couplings g0 = 1, g1, g2 ~ U[-1, 1]."""
+    rng = np.random.default_rng(seed)
+    lengths = np.exp(rng.uniform(np.log(lmin), np.log(lmax), size=nruns)).astype(np.int64)
+    couplings = np.column_stack([np.ones(nruns), rng.uniform(-1, 1, nruns), rng.uniform(-1, 1, nruns)])
+    parts = [boson_to_state(scattering_run(rng, int(L), eps), eps, dtype=dtype).ravel() for L in lengths]
+    return BatchWorkload("1d-batched-scattering-%druns" % nruns, lengths, couplings, eps, steps,
+                         32 if dtype == np.float32 else 64, np.concatenate(parts))

@@ -40,6 +40,14 @@ class QlgaObs(ctypes.Structure):
                 ("step", ctypes.c_int64)]
 
 
+class QlgaBatchConfig(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("nruns", ctypes.c_int32),
+                ("lengths", ctypes.POINTER(ctypes.c_int64)),
+                ("couplings", ctypes.POINTER(ctypes.c_double)),
+                ("epsilon", ctypes.c_double), ("kinetic_variant", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
+
+
 class QlgaError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__("%s failed: %s (%s)" % (where, _status_names.get(status, status), message))
@@ -70,6 +78,15 @@ _SIGNATURES = {
     "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
     "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_fields": [_H, _VP, ctypes.c_int],
+    "qlga_batch_state_bytes": [ctypes.POINTER(QlgaBatchConfig), ctypes.POINTER(ctypes.c_size_t)],
+    "qlga_batch_create": [ctypes.POINTER(QlgaBatchConfig), _VP, ctypes.POINTER(_H)],
+    "qlga_batch_load_state": [_H, _VP, ctypes.c_int],
+    "qlga_batch_get_state": [_H, _VP, ctypes.c_int],
+    "qlga_batch_step": [_H, ctypes.c_int64],
+    "qlga_batch_observables": [_H, ctypes.POINTER(QlgaObs)],
+    "qlga_batch_info": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int64)],
+    "qlga_batch_destroy": [_H],
     "qlga_destroy": [_H],
 }
 
@@ -342,3 +359,85 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------------ batches of 1D lattices
+
+def make_batch_config(lengths, couplings, precision=32, epsilon=0.1, kinetic_variant=0,
+                      use_graph=True):
+    """Returns (config, keepalive arrays) -- the arrays must outlive the create call."""
+    L = np.ascontiguousarray(lengths, dtype=np.int64)
+    G = np.ascontiguousarray(couplings, dtype=np.float64).reshape(len(L), 3)
+    cfg = QlgaBatchConfig(int(precision), len(L), L.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(epsilon),
+                          int(kinetic_variant), int(bool(use_graph)))
+    return cfg, (L, G)
+
+
+def qlga_batch_state_bytes(cfg) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().qlga_batch_state_bytes(ctypes.byref(cfg), ctypes.byref(out)),
+           "qlga_batch_state_bytes")
+    return out.value
+
+
+class Batch1D:
+    """Many periodic 1D lattices of uneven length, advanced together (one fused pass per step).
+
+    The state is the concatenation of the runs' 1D states in the library layout, as a flat
+    float32 / float64 array (see inputs.BatchWorkload)."""
+
+    def __init__(self, lengths, couplings, precision=32, epsilon=0.1, kinetic_variant=0,
+                 use_graph=True, stream=None):
+        import torch
+        self.lengths = np.asarray(lengths, dtype=np.int64)
+        self.nruns = len(self.lengths)
+        self.dtype = np.float32 if precision == 32 else np.float64
+        cfg, keep = make_batch_config(lengths, couplings, precision, epsilon, kinetic_variant,
+                                      use_graph)
+        if stream is None:
+            # graph capture needs a stream other than the legacy default stream
+            stream = torch.cuda.Stream() if use_graph else torch.cuda.current_stream()
+        self.stream = stream
+        h = _H()
+        _check(load_library().qlga_batch_create(ctypes.byref(cfg), _VP(self.stream.cuda_stream),
+                                                ctypes.byref(h)), "qlga_batch_create")
+        self.handle = h.value
+        self.nreals = int(self.lengths.sum()) * 20
+
+    def load_state(self, state):
+        a = np.ascontiguousarray(state, dtype=self.dtype).ravel()
+        assert a.size == self.nreals
+        _check(load_library().qlga_batch_load_state(_H(self.handle), _VP(a.ctypes.data), QLGA_HOST),
+               "qlga_batch_load_state")
+
+    def get_state(self):
+        out = np.empty(self.nreals, dtype=self.dtype)
+        _check(load_library().qlga_batch_get_state(_H(self.handle), _VP(out.ctypes.data), QLGA_HOST),
+               "qlga_batch_get_state")
+        return out
+
+    def step(self, n=1):
+        _check(load_library().qlga_batch_step(_H(self.handle), ctypes.c_int64(int(n))), "qlga_batch_step")
+
+    def observables(self):
+        arr = (QlgaObs * self.nruns)()
+        _check(load_library().qlga_batch_observables(_H(self.handle), arr), "qlga_batch_observables")
+        return [obs_to_dict(o) for o in arr]
+
+    def info(self):
+        w, l, g = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().qlga_batch_info(_H(self.handle), ctypes.byref(w), ctypes.byref(l),
+                                              ctypes.byref(g)), "qlga_batch_info")
+        return {"tile_width": w.value, "launches": l.value, "graph_steps": g.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load_library().qlga_batch_destroy(_H(self.handle)), "qlga_batch_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,101 @@
+"""Batches of 1D lattices (uneven lengths, per-run couplings) against the oracle, run by run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_12834_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1907_12834_gb300 import qlga  # noqa: E402
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def split(state, lengths):
+    out, o = [], 0
+    for L in lengths:
+        out.append(np.asarray(state[o:o + 20 * L]).reshape(5, 1, L, 2, 2))
+        o += 20 * L
+    return out
+
+
+def oracle_runs(state, lengths, couplings, nsteps, variant=0):
+    res = []
+    for st, L, g in zip(split(state, lengths), lengths, couplings):
+        r = np.ascontiguousarray(st, dtype=np.float64).copy()
+        oracle.step(r, oracle.make_cfg(1, int(L), 1, *g, kinetic_variant=variant), nsteps)
+        res.append(r)
+    return res
+
+
+LENGTHS = [8, 37, 64, 128, 129, 255, 1000, 2048, 3001]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ragged_batch_matches_oracle_per_run(precision, use_graph, variant):
+    rng = np.random.default_rng(53 + precision + variant)
+    couplings = np.column_stack([np.ones(len(LENGTHS)), rng.uniform(-1, 1, len(LENGTHS)),
+                                 rng.uniform(-1, 1, len(LENGTHS))])
+    state = np.concatenate([I.random_state(rng, L, scale=0.05).ravel() for L in LENGTHS])
+    state = state.astype(np.float32 if precision == 32 else np.float64)
+    b = qlga.Batch1D(LENGTHS, couplings, precision=precision, kinetic_variant=variant,
+                     use_graph=use_graph)
+    b.load_state(state)
+    n = 21                                              # odd: graph pairs plus a single step
+    b.step(n)
+    got = split(b.get_state(), LENGTHS)
+    info = b.info()
+    b.close()
+    ref = oracle_runs(state, LENGTHS, couplings, n, variant)
+    tol = 1e-11 if precision == 64 else 2e-5
+    for gr, rr in zip(got, ref):
+        assert rel_l2(gr, rr) <= tol
+    assert info["tile_width"] in (64, 128, 256)
+    assert (info["graph_steps"] > 0) == use_graph
+
+
+def test_batch_observables_per_run():
+    rng = np.random.default_rng(61)
+    couplings = np.column_stack([np.ones(len(LENGTHS)), rng.uniform(-1, 1, len(LENGTHS)),
+                                 rng.uniform(-1, 1, len(LENGTHS))])
+    state = np.concatenate([I.random_state(rng, L, scale=0.05).ravel() for L in LENGTHS])
+    b = qlga.Batch1D(LENGTHS, couplings, precision=64)
+    b.load_state(state)
+    b.step(4)
+    obs = b.observables()
+    cur = split(b.get_state(), LENGTHS)
+    b.close()
+    for o, st, L, g in zip(obs, cur, LENGTHS, couplings):
+        w = oracle.observables(np.ascontiguousarray(st), oracle.make_cfg(1, L, 1, *g))
+        for k in ("norm_qubit", "norm_boson", "magnetisation", "energy", "singlet_re", "singlet_im"):
+            assert abs(o[k] - w[k]) <= 1e-12 * w["norm_qubit"], k
+        np.testing.assert_allclose(o["pop"], w["pop"], rtol=0, atol=1e-12 * w["norm_qubit"])
+
+
+def test_config3_full_batch_sampled_runs():
+    """The 256-run batch (L log-uniform in [2048, 65536], per-run couplings) in FP32, 6 steps;
+    eight runs checked against the oracle, and every run's qubit norm against its start."""
+    w = I.config3()
+    b = qlga.Batch1D(w.lengths, w.couplings, precision=32)
+    b.load_state(w.state)
+    o0 = b.observables()
+    b.step(6)
+    got = b.get_state()
+    o1 = b.observables()
+    b.close()
+    runs = split(got, w.lengths)
+    for r in (0, 17, 64, 100, 128, 200, 254, 255):
+        ref = np.ascontiguousarray(w.run_state(r), dtype=np.float64).copy()
+        oracle.step(ref, oracle.make_cfg(1, int(w.lengths[r]), 1, *w.couplings[r]), 6)
+        assert rel_l2(runs[r], ref) <= 2e-5, r
+    for a, c in zip(o0, o1):
+        assert abs(c["norm_qubit"] - a["norm_qubit"]) <= 1e-5 * a["norm_qubit"]

@@ -19,6 +19,13 @@ Parity status of each function (what pins it; see tests/test_oracle_pins.py):
   observables       pinned: Table II characteristics, closed-form sums, brute force.
   fields            pinned: Table II characteristics per site, plane-wave velocity (zero
                     vorticity), total vorticity of a vortex / antivortex (+-2 pi), colour norm.
+  frechet_exp       pinned: block-triangular exponential exp([[A, E], [0, A]]) (scipy).
+  vjp_kinetic       pinned: dot-product identity <K v, w> = <v, K^dagger w>, K^dagger K = 1.
+  vjp_potential /   pinned: central finite differences of the (pinned) forward operators in
+  vjp_step / run    random directions, coupling derivatives by finite differences in g.
+
+Adjoint cotangents: for a real loss L the cotangent array has the state's shape and holds
+dL/d(each real component); dL = sum(cot * dx).
 """
 from __future__ import annotations
 
@@ -117,9 +124,16 @@ class Oracle:
         lib.oracle_expm.argtypes = [dp, ctypes.c_double, dp]
         lib.oracle_max_threads.argtypes = []
         lib.oracle_fields.argtypes = [dp, cp, dp]
+        lib.oracle_vjp_potential.argtypes = [dp, dp, cp, ctypes.c_double, dp, ctypes.c_int]
+        lib.oracle_vjp_kinetic.argtypes = [dp, cp, ctypes.c_int]
+        lib.oracle_vjp_step.argtypes = [dp, dp, cp, dp, ctypes.c_int]
+        lib.oracle_vjp_run.argtypes = [dp, ctypes.c_long, dp, cp, dp, ctypes.c_int]
+        lib.oracle_frechet_exp.argtypes = [dp, ctypes.c_double, dp, dp]
         for name in ("oracle_step", "oracle_apply_potential", "oracle_apply_kinetic",
                      "oracle_apply_operator", "oracle_observables", "oracle_potential_matrix",
-                     "oracle_heig", "oracle_expm", "oracle_max_threads", "oracle_fields"):
+                     "oracle_heig", "oracle_expm", "oracle_max_threads", "oracle_fields",
+                     "oracle_vjp_potential", "oracle_vjp_kinetic", "oracle_vjp_step",
+                     "oracle_vjp_run", "oracle_frechet_exp"):
             getattr(lib, name).restype = ctypes.c_int
         self.lib = lib
         self.path = path
@@ -197,6 +211,52 @@ class Oracle:
         self.lib.oracle_expm(_dptr(_mat_to_buf(V)), float(delta), _dptr(U))
         return (U[0::2] + 1j * U[1::2]).reshape(5, 5)
 
+    # ------------------------------------------------------------ adjoint
+    def vjp_potential(self, state, cot, cfg, delta=1.0, nthreads=0):
+        """cot (cotangent of U(x) x) -> cotangent of x, in place; returns dL/d(g0, g1, g2)."""
+        _check_state(state, cfg)
+        _check_state(cot, cfg)
+        d = np.zeros(3)
+        if self.lib.oracle_vjp_potential(_dptr(state), _dptr(cot), ctypes.byref(cfg), float(delta),
+                                         _dptr(d), int(nthreads)):
+            raise ValueError("bad arguments")
+        return d
+
+    def vjp_kinetic(self, field, cfg, nthreads=0):
+        """field <- K^dagger field, in place."""
+        _check_state(field, cfg)
+        if self.lib.oracle_vjp_kinetic(_dptr(field), ctypes.byref(cfg), int(nthreads)):
+            raise ValueError("bad arguments")
+        return field
+
+    def vjp_step(self, state, cot, cfg, nthreads=0):
+        """cot (cotangent of step(x)) -> cotangent of x, in place; returns dL/d(g0, g1, g2)."""
+        _check_state(state, cfg)
+        _check_state(cot, cfg)
+        d = np.zeros(3)
+        rc = self.lib.oracle_vjp_step(_dptr(state), _dptr(cot), ctypes.byref(cfg), _dptr(d), int(nthreads))
+        if rc:
+            raise ValueError("oracle_vjp_step rejected its arguments (%d)" % rc)
+        return d
+
+    def vjp_run(self, x0, nsteps, cot, cfg, nthreads=0):
+        """Gradient through nsteps plain steps from x0: cot (cotangent of the final state) ->
+        cotangent of x0, in place; returns dL/d(g0, g1, g2)."""
+        _check_state(x0, cfg)
+        _check_state(cot, cfg)
+        d = np.zeros(3)
+        rc = self.lib.oracle_vjp_run(_dptr(x0), int(nsteps), _dptr(cot), ctypes.byref(cfg), _dptr(d),
+                                     int(nthreads))
+        if rc:
+            raise ValueError("oracle_vjp_run rejected its arguments (%d)" % rc)
+        return d
+
+    def frechet_exp(self, V, delta, E) -> np.ndarray:
+        """L(-i delta V, E): the Frechet derivative of exp at -i delta V in direction E."""
+        out = np.zeros(50)
+        self.lib.oracle_frechet_exp(_dptr(_mat_to_buf(V)), float(delta), _dptr(_mat_to_buf(E)), _dptr(out))
+        return (out[0::2] + 1j * out[1::2]).reshape(5, 5)
+
 
 _default = None
 
@@ -246,6 +306,26 @@ def heig(V):
 
 def expm(V, delta):
     return default().expm(V, delta)
+
+
+def vjp_potential(state, cot, cfg, delta=1.0, nthreads=0):
+    return default().vjp_potential(state, cot, cfg, delta, nthreads)
+
+
+def vjp_kinetic(field, cfg, nthreads=0):
+    return default().vjp_kinetic(field, cfg, nthreads)
+
+
+def vjp_step(state, cot, cfg, nthreads=0):
+    return default().vjp_step(state, cot, cfg, nthreads)
+
+
+def vjp_run(x0, nsteps, cot, cfg, nthreads=0):
+    return default().vjp_run(x0, nsteps, cot, cfg, nthreads)
+
+
+def frechet_exp(V, delta, E):
+    return default().frechet_exp(V, delta, E)
 
 
 def source_text() -> str:

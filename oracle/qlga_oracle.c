@@ -211,9 +211,7 @@ static void apply_potential(double* st, const oracle_cfg* cfg, double delta) {
 
 /* The 2x2 collide on every qubit pair (a_m, b_m).  which = 0: the collide C of the
  * variant; which = 1: the second collide of a block (C for K1, C^dagger for K2). */
-static void collide(double* st, const oracle_cfg* cfg, int which) {
-    const long n = cfg->nx * cfg->ny;
-    cplx C[2][2];
+static void collide_matrix(const oracle_cfg* cfg, int which, cplx C[2][2]) {
     if (cfg->kinetic_variant == 0 || which == 1) {
         C[0][0] = 0.5 * (1.0 - I); C[0][1] = 0.5 * (1.0 + I);
         C[1][0] = 0.5 * (1.0 + I); C[1][1] = 0.5 * (1.0 - I);
@@ -222,6 +220,20 @@ static void collide(double* st, const oracle_cfg* cfg, int which) {
         C[1][0] = 0.5 * (1.0 - I); C[1][1] = 0.5 * (1.0 + I);
     }
     /* K1 uses C twice; K2 uses C then C^dagger, and C_K2^dagger equals C_K1. */
+}
+
+/* adjoint = 1 applies the conjugate transpose of the collide instead. */
+static void collide_any(double* st, const oracle_cfg* cfg, int which, int adjoint) {
+    const long n = cfg->nx * cfg->ny;
+    cplx C[2][2];
+    collide_matrix(cfg, which, C);
+    if (adjoint) {
+        const cplx c01 = C[0][1];
+        C[0][0] = conj(C[0][0]);
+        C[1][1] = conj(C[1][1]);
+        C[0][1] = conj(C[1][0]);
+        C[1][0] = conj(c01);
+    }
 #pragma omp parallel for schedule(static)
     for (long site = 0; site < n; ++site)
         for (int m = 0; m < 5; ++m) {
@@ -232,6 +244,8 @@ static void collide(double* st, const oracle_cfg* cfg, int which) {
             putc_(pb, C[1][0] * a + C[1][1] * b);
         }
 }
+
+static void collide(double* st, const oracle_cfg* cfg, int which) { collide_any(st, cfg, which, 0); }
 
 /* Stream qubit q of every level one site along `axis` (0 = x, 1 = y):
  * dir = +1 is S_q, q(j) <- q(j-1); dir = -1 is S^T_q, q(j) <- q(j+1).  Periodic. */
@@ -286,6 +300,184 @@ static void step_once(double* st, const oracle_cfg* cfg) {
             apply_potential(st, cfg, frac);
             kinetic_block(st, cfg, axis, block_qubit[k]);
         }
+}
+
+/* ---------------------------------------------------------------- adjoint (reverse mode)
+ *
+ * Pull-back of a cotangent through the plain step x' = K U(x) x (Sec. VII.B), for gradients of a
+ * real loss L.  The cotangent of a complex amplitude z is gbar = dL/dRe z + i dL/dIm z, so that
+ * dL = Re sum conj(gbar) dz; in the state layout it is stored like the state.
+ *
+ * Kinetic part.  K is complex-linear and unitary, so gbar_x = K^dagger gbar_x'.  K^dagger runs the
+ * axes in reverse order (y, then x) and on each axis the blocks in reverse order; the adjoint of a
+ * block S_c C' S^T_c C is C^dagger S_c C'^dagger S^T_c (S^T_c acts first).
+ *
+ * Potential part.  a' = U a, b' = U b with U = exp(A), A = -i delta V(psi), psi = a + b.  Then
+ *   gbar_a = U^dagger gbar_a' + h,   gbar_b = U^dagger gbar_b' + h,
+ * where h carries the dependence of V on psi.  With Mt = a gbar_a'^dagger + b gbar_b'^dagger, the
+ * change of L through dU is Re tr(dU Mt); dU = L(A, dA) is the Frechet derivative of exp, and
+ * tr(L(A, E) Mt) = tr(E L(A, Mt)), so with G = L(A, Mt) and the Hermitian H = (G - G^dagger)/(2i):
+ *   dL = delta tr(dV H)   (dV Hermitian).
+ * dV = g0 drho 1 + g1 sum_nu dF_nu f_nu + (g2/5)(ds s^dagger + s ds^dagger), drho = 2 Re psi^dagger dpsi,
+ * dF_nu = 2 Re psi^dagger f_nu dpsi, ds = J conj(dpsi), give
+ *   h = delta [2 g0 tr(H) psi + 2 g1 sum_nu tr(f_nu H) f_nu psi + (2 g2/5) J conj(H s)],
+ * and the coupling gradients delta rho tr(H), delta sum_nu F_nu tr(f_nu H), (delta/5) s^dagger H s.
+ * L(A, E) is taken in the eigenbasis of V (Daleckii-Krein): with V = Q diag(lambda) Q^dagger,
+ * (Q^dagger L(A, E) Q)_ij = (Q^dagger E Q)_ij phi_ij, phi_ij the divided difference of
+ * exp(-i delta lambda) at lambda_i, lambda_j: exp(-i delta (lambda_i + lambda_j)/2) sinc(delta
+ * (lambda_i - lambda_j)/2), which is exp(-i delta lambda_i) when they coincide.
+ */
+
+static cplx divided_difference_exp(double li, double lj, double delta) {
+    const double x = 0.5 * delta * (li - lj);
+    const double sinc = (x == 0.0) ? 1.0 : sin(x) / x;
+    return cexp(-I * delta * 0.5 * (li + lj)) * sinc;
+}
+
+/* L(-i delta V, E) for Hermitian V (the Frechet derivative of exp at A = -i delta V). */
+static void frechet_exp_herm(const cplx V[5][5], double delta, const cplx E[5][5], cplx Lout[5][5]) {
+    cplx A[5][5], Q[5][5], T[5][5], Et[5][5];
+    double lam[5];
+    memcpy(A, V, sizeof(A));
+    herm_eig(A, lam, Q);
+    for (int i = 0; i < 5; ++i) /* T = E Q */
+        for (int j = 0; j < 5; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += E[i][k] * Q[k][j];
+            T[i][j] = acc;
+        }
+    for (int i = 0; i < 5; ++i) /* Et = (Q^dagger E Q) o phi */
+        for (int j = 0; j < 5; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += conj(Q[k][i]) * T[k][j];
+            Et[i][j] = acc * divided_difference_exp(lam[i], lam[j], delta);
+        }
+    for (int i = 0; i < 5; ++i) /* T = Q Et */
+        for (int j = 0; j < 5; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += Q[i][k] * Et[k][j];
+            T[i][j] = acc;
+        }
+    for (int i = 0; i < 5; ++i) /* L = T Q^dagger */
+        for (int j = 0; j < 5; ++j) {
+            cplx acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += T[i][k] * conj(Q[j][k]);
+            Lout[i][j] = acc;
+        }
+}
+
+/* The pull-back through U at one site: (ga, gb) hold the cotangents of (a', b') on entry and
+ * those of (a, b) on exit; dcoup[3] accumulates dL/d(g0, g1, g2). */
+static void potential_vjp_site(const cplx a[5], const cplx b[5], cplx ga[5], cplx gb[5],
+                               const oracle_cfg* cfg, double delta, double dcoup[3]) {
+    cplx psi[5], V[5][5], U[5][5], Mt[5][5], G[5][5], H[5][5];
+    cplx fx[5][5], fy[5][5], fz[5][5];
+    spin2_matrices(fx, fy, fz);
+    cplx (*f[3])[5] = {fx, fy, fz};
+    for (int m = 0; m < 5; ++m) psi[m] = a[m] + b[m];
+    potential_matrix(psi, cfg->g0, cfg->g1, cfg->g2, V);
+    expm_herm(V, delta, U);
+    cplx pa[5], pb[5]; /* U^dagger applied to the incoming cotangents */
+    for (int i = 0; i < 5; ++i) {
+        pa[i] = 0.0;
+        pb[i] = 0.0;
+        for (int j = 0; j < 5; ++j) {
+            pa[i] += conj(U[j][i]) * ga[j];
+            pb[i] += conj(U[j][i]) * gb[j];
+        }
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) Mt[i][j] = a[i] * conj(ga[j]) + b[i] * conj(gb[j]);
+    frechet_exp_herm(V, delta, Mt, G);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) H[i][j] = (G[i][j] - conj(G[j][i])) / (2.0 * I);
+    double rho = 0.0, trH = 0.0, F[3], trfH[3];
+    for (int i = 0; i < 5; ++i) {
+        rho += creal(conj(psi[i]) * psi[i]);
+        trH += creal(H[i][i]);
+    }
+    for (int nu = 0; nu < 3; ++nu) {
+        cplx fv = 0.0, tr = 0.0;
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                fv += conj(psi[i]) * f[nu][i][j] * psi[j];
+                tr += f[nu][i][j] * H[j][i];
+            }
+        F[nu] = creal(fv);
+        trfH[nu] = creal(tr);
+    }
+    cplx s[5], Hs[5], sHs = 0.0;
+    for (int i = 0; i < 5; ++i) {
+        const int m = 2 - i;
+        s[i] = ((m % 2 == 0) ? 1.0 : -1.0) * conj(psi[4 - i]);
+    }
+    for (int i = 0; i < 5; ++i) {
+        Hs[i] = 0.0;
+        for (int j = 0; j < 5; ++j) Hs[i] += H[i][j] * s[j];
+    }
+    for (int i = 0; i < 5; ++i) sHs += conj(s[i]) * Hs[i];
+    for (int i = 0; i < 5; ++i) {
+        cplx h = 2.0 * cfg->g0 * trH * psi[i];
+        for (int nu = 0; nu < 3; ++nu)
+            for (int j = 0; j < 5; ++j) h += 2.0 * cfg->g1 * trfH[nu] * f[nu][i][j] * psi[j];
+        const int m = 2 - i;
+        h += (2.0 * cfg->g2 / 5.0) * ((m % 2 == 0) ? 1.0 : -1.0) * conj(Hs[4 - i]);
+        h *= delta;
+        ga[i] = pa[i] + h;
+        gb[i] = pb[i] + h;
+    }
+    dcoup[0] += delta * rho * trH;
+    dcoup[1] += delta * (F[0] * trfH[0] + F[1] * trfH[1] + F[2] * trfH[2]);
+    dcoup[2] += delta * creal(sHs) / 5.0;
+}
+
+/* st: the state x before U; cot: cotangent of U(x) x on entry, of x on exit. */
+static void potential_vjp(const double* st, double* cot, const oracle_cfg* cfg, double delta,
+                          double dcoup[3]) {
+    const long n = cfg->nx * cfg->ny;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : d0, d1, d2)
+    for (long site = 0; site < n; ++site) {
+        cplx a[5], b[5], ga[5], gb[5];
+        double dc[3] = {0.0, 0.0, 0.0};
+        for (int m = 0; m < 5; ++m) {
+            a[m] = getc(amp((double*)st, n, m, site, 0));
+            b[m] = getc(amp((double*)st, n, m, site, 1));
+            ga[m] = getc(amp(cot, n, m, site, 0));
+            gb[m] = getc(amp(cot, n, m, site, 1));
+        }
+        potential_vjp_site(a, b, ga, gb, cfg, delta, dc);
+        for (int m = 0; m < 5; ++m) {
+            putc_(amp(cot, n, m, site, 0), ga[m]);
+            putc_(amp(cot, n, m, site, 1), gb[m]);
+        }
+        d0 += dc[0];
+        d1 += dc[1];
+        d2 += dc[2];
+    }
+    dcoup[0] += d0;
+    dcoup[1] += d1;
+    dcoup[2] += d2;
+}
+
+/* K^dagger applied to a cotangent (or any field): axes, blocks and factors in reverse order,
+ * each factor replaced by its adjoint. */
+static void kinetic_block_adjoint(double* st, const oracle_cfg* cfg, int axis, int q) {
+    stream(st, cfg, axis, q, -1);     /* (S_c)^dagger = S^T_c */
+    collide_any(st, cfg, 1, 1);       /* C'^dagger */
+    stream(st, cfg, axis, q, +1);     /* (S^T_c)^dagger = S_c */
+    collide_any(st, cfg, 0, 1);       /* C^dagger */
+}
+
+static void apply_kinetic_adjoint(double* st, const oracle_cfg* cfg) {
+    for (int axis = cfg->ndim - 1; axis >= 0; --axis)
+        for (int k = 3; k >= 0; --k) kinetic_block_adjoint(st, cfg, axis, block_qubit[k]);
+}
+
+/* One plain step pulled back: cot <- (d step / d x)^T cot at the state x. */
+static void vjp_step(const double* x, double* cot, const oracle_cfg* cfg, double dcoup[3]) {
+    apply_kinetic_adjoint(cot, cfg);
+    potential_vjp(x, cot, cfg, 1.0, dcoup);
 }
 
 /* ---------------------------------------------------------------- observables */
@@ -522,6 +714,71 @@ int oracle_expm(const double* V50, double delta, double* U50) {
 int oracle_fields(const double* state, const oracle_cfg* cfg, double* out11) {
     if (!cfg_ok(cfg) || !state || !out11) return 1;
     fields(state, cfg, out11);
+    return 0;
+}
+
+/* Adjoint entry points (plain step only; the interleaved step returns 2).
+ * oracle_vjp_potential: cot (cotangent of U(x) x) -> cotangent of x at state x, with delta.
+ * oracle_vjp_kinetic:   field <- K^dagger field.
+ * oracle_vjp_step:      cot (cotangent of step(x)) -> cotangent of x.
+ * oracle_vjp_run:       forward nsteps from x0 keeping every state, then pull cot (cotangent of
+ *                       the final state) back to the cotangent of x0.
+ * dcoup3 accumulates dL/d(g0, g1, g2). */
+int oracle_vjp_potential(const double* x, double* cot, const oracle_cfg* cfg, double delta,
+                         double* dcoup3, int nthreads) {
+    if (!cfg_ok(cfg) || !x || !cot || !dcoup3) return 1;
+    set_threads(nthreads);
+    potential_vjp(x, cot, cfg, delta, dcoup3);
+    return 0;
+}
+
+int oracle_vjp_kinetic(double* field, const oracle_cfg* cfg, int nthreads) {
+    if (!cfg_ok(cfg) || !field) return 1;
+    set_threads(nthreads);
+    apply_kinetic_adjoint(field, cfg);
+    return 0;
+}
+
+int oracle_vjp_step(const double* x, double* cot, const oracle_cfg* cfg, double* dcoup3, int nthreads) {
+    if (!cfg_ok(cfg) || !x || !cot || !dcoup3) return 1;
+    if (cfg->interleave) return 2;
+    set_threads(nthreads);
+    vjp_step(x, cot, cfg, dcoup3);
+    return 0;
+}
+
+int oracle_vjp_run(const double* x0, long nsteps, double* cot, const oracle_cfg* cfg,
+                   double* dcoup3, int nthreads) {
+    if (!cfg_ok(cfg) || !x0 || !cot || !dcoup3 || nsteps < 0) return 1;
+    if (cfg->interleave) return 2;
+    set_threads(nthreads);
+    const size_t len = (size_t)(cfg->nx * cfg->ny) * 20;
+    double* hist = (double*)malloc(sizeof(double) * len * (size_t)(nsteps > 0 ? nsteps : 1));
+    if (!hist) return 3;
+    if (nsteps > 0) memcpy(hist, x0, sizeof(double) * len);
+    for (long k = 1; k < nsteps; ++k) {
+        memcpy(hist + k * len, hist + (k - 1) * len, sizeof(double) * len);
+        step_once(hist + k * len, cfg);
+    }
+    for (long k = nsteps - 1; k >= 0; --k) vjp_step(hist + k * len, cot, cfg, dcoup3);
+    free(hist);
+    return 0;
+}
+
+/* L(-i delta V, E) for Hermitian V; V50, E50, L50: 5x5 complex row-major (re, im). */
+int oracle_frechet_exp(const double* V50, double delta, const double* E50, double* L50) {
+    cplx V[5][5], E[5][5], Lm[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            V[i][j] = V50[2 * (5 * i + j)] + I * V50[2 * (5 * i + j) + 1];
+            E[i][j] = E50[2 * (5 * i + j)] + I * E50[2 * (5 * i + j) + 1];
+        }
+    frechet_exp_herm(V, delta, E, Lm);
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            L50[2 * (5 * i + j)] = creal(Lm[i][j]);
+            L50[2 * (5 * i + j) + 1] = cimag(Lm[i][j]);
+        }
     return 0;
 }
 

@@ -321,3 +321,163 @@ def pin_fields(orc):
     for h in (4, 12):
         worst = max(worst, abs(box(cx - 20, h) - 2 * np.pi), abs(box(cx + 20, h) + 2 * np.pi))
     return worst
+
+
+# ----------------------------------------------------------------- adjoint (reverse mode)
+
+def _rand_state(rng, ndim, nx, ny, amp=0.35):
+    shape = (5, ny, nx, 2, 2)
+    return np.ascontiguousarray(amp * rng.standard_normal(shape))
+
+
+def pin_frechet(orc, trials=12, seed=11):
+    """max relative deviation of L(-i delta V, E) from the upper-right block of
+    exp([[A, E], [0, A]]) with A = -i delta V (the block-triangular identity for the Frechet
+    derivative of the matrix exponential), scipy's expm.  V: random Hermitian matrices, the
+    potential of random sites, and a degenerate V (repeated eigenvalues)."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    cases = []
+    for t in range(trials):
+        X = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+        cases.append((0.5 * (X + X.conj().T), 0.3 + 0.2 * t))
+        psi = 0.6 * (rng.standard_normal(5) + 1j * rng.standard_normal(5))
+        cases.append((orc.potential_matrix(psi, 1.0, -0.5 + 0.1 * t, 0.7 - 0.15 * t), 1.0))
+    cases.append((np.diag([1.0, 1.0, -0.5, 2.0, 2.0]).astype(complex), 1.0))
+    for V, delta in cases:
+        E = rng.standard_normal((5, 5)) + 1j * rng.standard_normal((5, 5))
+        A = -1j * delta * V
+        big = np.zeros((10, 10), dtype=complex)
+        big[:5, :5] = A
+        big[5:, 5:] = A
+        big[:5, 5:] = E
+        ref = sl.expm(big)[:5, 5:]
+        got = orc.frechet_exp(V, delta, E)
+        worst = max(worst, float(np.abs(got - ref).max() / np.abs(ref).max()))
+    return worst
+
+
+def _dot(u, v):
+    return float(np.sum(u * v))
+
+
+def pin_kinetic_adjoint(orc):
+    """max relative violation of <K v, w> = <v, K^dagger w> (real inner product of the state
+    buffers, i.e. Re sum conj(x) y) and of K^dagger K v = v (K is unitary), 1D and 2D, K1/K2."""
+    rng = np.random.default_rng(5)
+    worst = 0.0
+    for ndim, nx, ny in ((1, 12, 1), (2, 7, 6)):
+        for variant in (0, 1):
+            cfg = oracle.make_cfg(ndim, nx, ny, 1.0, 0.2, 0.3, kinetic_variant=variant)
+            v = _rand_state(rng, ndim, nx, ny)
+            w = _rand_state(rng, ndim, nx, ny)
+            Kv = orc.apply_kinetic(v.copy(), cfg)
+            Ktw = orc.vjp_kinetic(w.copy(), cfg)
+            lhs, rhs = _dot(Kv, w), _dot(v, Ktw)
+            worst = max(worst, abs(lhs - rhs) / (np.linalg.norm(v) * np.linalg.norm(w)))
+            back = orc.vjp_kinetic(Kv.copy(), cfg)
+            worst = max(worst, float(np.abs(back - v).max()))
+    return worst
+
+
+def _fd_directional(fwd, x, v, h):
+    """Central difference of the map fwd at x in direction v (fourth order: two step sizes)."""
+    d1 = (fwd(x + h * v) - fwd(x - h * v)) / (2 * h)
+    d2 = (fwd(x + 2 * h * v) - fwd(x - 2 * h * v)) / (4 * h)
+    return (4 * d1 - d2) / 3
+
+
+ADJ_CASES = [  # (ndim, nx, ny, (g0, g1, g2), variant)
+    (1, 10, 1, (1.0, -0.5, 0.2), 0),
+    (1, 9, 1, (1.0, 0.8, -0.6), 1),
+    (2, 6, 5, (1.0, 0.1, 1.0), 0),
+    (2, 5, 6, (0.7, -0.4, 0.9), 1),
+]
+
+
+def pin_vjp_fd(orc, what="step", nsteps=3, seed=21):
+    """max relative deviation between <vjp(w), v> and <w, J v>, J v the central finite
+    difference of the forward map in a random direction v, for w a random cotangent.
+    what: "potential" (U alone, delta = 1 and 1/4), "step" (one plain step) or "run" (nsteps
+    plain steps through vjp_run).  The forward operators are pinned independently."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for ndim, nx, ny, g, variant in ADJ_CASES:
+        cfg = oracle.make_cfg(ndim, nx, ny, *g, kinetic_variant=variant)
+        x = _rand_state(rng, ndim, nx, ny)
+        v = _rand_state(rng, ndim, nx, ny, amp=1.0)
+        w = _rand_state(rng, ndim, nx, ny, amp=1.0)
+        deltas = (1.0, 0.25) if what == "potential" else (1.0,)
+        for delta in deltas:
+            if what == "potential":
+                fwd = lambda s: orc.apply_potential(np.ascontiguousarray(s), cfg, delta)
+                cot = w.copy()
+                orc.vjp_potential(x, cot, cfg, delta)
+            elif what == "step":
+                fwd = lambda s: orc.step(np.ascontiguousarray(s), cfg, 1)
+                cot = w.copy()
+                orc.vjp_step(x, cot, cfg)
+            else:
+                fwd = lambda s: orc.step(np.ascontiguousarray(s), cfg, nsteps)
+                cot = w.copy()
+                orc.vjp_run(x, nsteps, cot, cfg)
+            jv = _fd_directional(fwd, x, v, 1e-5)
+            lhs, rhs = _dot(w, jv), _dot(cot, v)
+            worst = max(worst, abs(lhs - rhs) / max(abs(lhs), 1e-3 * np.linalg.norm(w) * np.linalg.norm(v)))
+    return worst
+
+
+def pin_coupling_fd(orc, nsteps=3, seed=23):
+    """max relative deviation of dL/dg from vjp_run against central finite differences in each
+    coupling, L = <w, x_n> for a random cotangent w."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for ndim, nx, ny, g, variant in ADJ_CASES:
+        x = _rand_state(rng, ndim, nx, ny)
+        w = _rand_state(rng, ndim, nx, ny, amp=1.0)
+        cfg = oracle.make_cfg(ndim, nx, ny, *g, kinetic_variant=variant)
+        cot = w.copy()
+        dg = orc.vjp_run(x, nsteps, cot, cfg)
+
+        def loss(gv):
+            c = oracle.make_cfg(ndim, nx, ny, *gv, kinetic_variant=variant)
+            return _dot(w, orc.step(x.copy(), c, nsteps))
+
+        h = 1e-5
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = 1.0
+            gp = np.array(g)
+            d1 = (loss(gp + h * e) - loss(gp - h * e)) / (2 * h)
+            d2 = (loss(gp + 2 * h * e) - loss(gp - 2 * h * e)) / (4 * h)
+            fd = (4 * d1 - d2) / 3
+            worst = max(worst, abs(fd - dg[i]) / max(abs(fd), 1e-3))
+    return worst
+
+
+def pin_tf_coupling_gradient(orc):
+    """Closed form: a uniform single-level state psi = (c, 0, 0, 0, 0) with a = b = psi/2 is an
+    eigenvector of V with eigenvalue (g0 + 4 g1) rho and is left alone by the kinetic operator
+    (zero momentum), so one step is x' = exp(-i (g0 + 4 g1) rho) x.  For L = <w, x'>:
+    dL/dg0 = <w, -i rho x'>, dL/dg1 = 4 dL/dg0, dL/dg2 = 0.  Returns the max relative deviation."""
+    rng = np.random.default_rng(29)
+    worst = 0.0
+    for ndim, nx, ny in ((1, 8, 1), (2, 6, 6)):
+        for g in ((1.0, -0.5, 0.2), (0.6, 0.3, -0.8)):
+            cfg = oracle.make_cfg(ndim, nx, ny, *g)
+            c = 0.45 * np.exp(0.7j)
+            x = np.zeros((5, ny, nx, 2, 2))
+            x[0, :, :, :, 0] = c.real / 2
+            x[0, :, :, :, 1] = c.imag / 2
+            rho = abs(c) ** 2
+            theta = (g[0] + 4 * g[1]) * rho
+            xc = x[..., 0] + 1j * x[..., 1]
+            xp = np.exp(-1j * theta) * xc
+            w = rng.standard_normal(x.shape)
+            wc = w[..., 0] + 1j * w[..., 1]
+            dg0 = float(np.sum((np.conj(wc) * (-1j * rho) * xp).real))
+            cot = w.copy()
+            dg = orc.vjp_step(x, cot, cfg)
+            ref = np.array([dg0, 4 * dg0, 0.0])
+            worst = max(worst, float(np.abs(dg - ref).max() / abs(dg0)))
+    return worst

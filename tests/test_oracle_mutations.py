@@ -25,7 +25,7 @@ MUTATIONS = [
     ("collide_transposed", "C[0][0] = 0.5 * (1.0 - I); C[0][1] = 0.5 * (1.0 + I);",
      "C[0][0] = 0.5 * (1.0 + I); C[0][1] = 0.5 * (1.0 - I);",
      lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
-    ("potential_uses_a_only", "psi[m] = a[m] + b[m];", "psi[m] = a[m] + a[m];",
+    ("potential_uses_a_only", "\n            psi[m] = a[m] + b[m];", "\n            psi[m] = a[m] + a[m];",
      lambda o: pins.pin_dense_step(o, 2), 1e-13),
     ("y_stream_on_x", "else sy = ((y - dir) % ny + ny) % ny;", "else sx = ((x - dir) % nx + nx) % nx;",
      lambda o: pins.pin_plane_wave_symbol(o), 1e-13),
@@ -33,6 +33,27 @@ MUTATIONS = [
      lambda o: pins.pin_fields(o), 1e-12),
     ("interleave_fraction", "const double frac = 1.0 / (4.0 * cfg->ndim);",
      "const double frac = 1.0 / 4.0;", lambda o: pins.pin_dense_step(o, 2, interleave=1), 1e-13),
+    # adjoint
+    ("frechet_phase_sign", "cexp(-I * delta * 0.5 * (li + lj))", "cexp(I * delta * 0.5 * (li + lj))",
+     lambda o: pins.pin_frechet(o), 1e-12),
+    ("adjoint_stream_direction", "stream(st, cfg, axis, q, -1);     /* (S_c)^dagger",
+     "stream(st, cfg, axis, q, +1);     /* (S_c)^dagger", lambda o: pins.pin_kinetic_adjoint(o), 1e-13),
+    ("adjoint_collide_not_conjugated", "collide_any(st, cfg, 0, 1);       /* C^dagger */",
+     "collide_any(st, cfg, 0, 0);       /* C^dagger */", lambda o: pins.pin_kinetic_adjoint(o), 1e-13),
+    ("adjoint_axes_forward_order", "for (int axis = cfg->ndim - 1; axis >= 0; --axis)\n        for (int k = 3;",
+     "for (int axis = 0; axis < cfg->ndim; ++axis)\n        for (int k = 3;", lambda o: pins.pin_kinetic_adjoint(o), 1e-13),
+    ("adjoint_H_hermitian_part", "H[i][j] = (G[i][j] - conj(G[j][i])) / (2.0 * I);",
+     "H[i][j] = (G[i][j] + conj(G[j][i])) / 2.0;", lambda o: pins.pin_vjp_fd(o, "potential"), 1e-8),
+    ("adjoint_singlet_dropped", "h += (2.0 * cfg->g2 / 5.0) *", "h += 0.0 * (2.0 * cfg->g2 / 5.0) *",
+     lambda o: pins.pin_vjp_fd(o, "potential"), 1e-8),
+    ("adjoint_spin_half", "h += 2.0 * cfg->g1 * trfH[nu]", "h += cfg->g1 * trfH[nu]",
+     lambda o: pins.pin_vjp_fd(o, "step"), 1e-8),
+    ("adjoint_missing_U_dagger", "pa[i] += conj(U[j][i]) * ga[j];", "pa[i] += U[j][i] * ga[j];",
+     lambda o: pins.pin_vjp_fd(o, "potential"), 1e-8),
+    ("adjoint_psi_uses_a_only", "++m) psi[m] = a[m] + b[m];", "++m) psi[m] = a[m] + a[m];",
+     lambda o: pins.pin_vjp_fd(o, "potential"), 1e-8),
+    ("coupling_g2_fifth", "dcoup[2] += delta * creal(sHs) / 5.0;", "dcoup[2] += delta * creal(sHs);",
+     lambda o: pins.pin_coupling_fd(o), 1e-7),
 ]
 
 

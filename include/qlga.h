@@ -194,6 +194,56 @@ qlga_status qlga_synchronize(qlga_handle* h);
 qlga_status qlga_destroy(qlga_handle* h);
 
 /* ---------------------------------------------------------------------------------------
+ * Adjoint (reverse mode): gradients of a real loss L of the state after n plain steps
+ * x_{k+1} = K U(x_k) x_k (Sec. VII.B), with respect to the initial state x_0 and the couplings
+ * (g0, g1, g2) of Eq. hamspin2.
+ *
+ * Cotangents.  A cotangent buffer has the state layout and precision above and holds
+ * dL/d(each real of the state): element (m, y, x, q, c) is dL/d(Re or Im of a or b).  So
+ * dL = sum over all elements of cot * dx.  One step pulls a cotangent back as
+ * cot_k = (d x_{k+1} / d x_k)^T cot_{k+1}: the adjoint kinetic operator K^dagger (axes and blocks
+ * in reverse order, each collide and stream replaced by its adjoint), then the transposed
+ * linearisation of U at x_k, which includes the dependence of V on psi = a + b (Frechet
+ * derivative of exp(-i delta V), evaluated with the forward step's own Taylor degree).
+ *
+ * Checkpoints.  qlga_adjoint_forward() keeps the true state every C steps (x_0, x_C, ...) in the
+ * workspace; qlga_adjoint_backward() recomputes each segment of C states from its checkpoint
+ * (C extra state buffers) and pulls the cotangent back through it.  Checkpoints are held in the
+ * handle's precision: a recomputed segment repeats the forward arithmetic of that precision.
+ * Workspace: qlga_adjoint_workspace_bytes() bytes of device memory, 256-byte aligned, owned by
+ * the caller; about (ceil(n / C) + C + 4) state buffers.  The same workspace must be passed to
+ * the forward and the backward call of one run, unchanged in between.
+ *
+ * The adjoint covers the plain step only: a handle with interleave = 1 gets
+ * QLGA_ERR_UNSUPPORTED.  dcoup (host, 3 doubles) receives dL/d(g0, g1, g2) and may be NULL.
+ * All three calls enqueue on the handle's stream; backward and step wait for it before
+ * returning (they read dcoup back).  A status word set by U (exponent out of range) is reported
+ * as QLGA_ERR_NOT_FINITE, as for the forward step. */
+qlga_status qlga_adjoint_workspace_bytes(const qlga_config* cfg, int64_t nsteps, int64_t checkpoint_every,
+                                         size_t* bytes);
+
+/* Load x0 (device, state layout) into the handle, advance it nsteps plain steps (the handle ends
+ * holding x_n, as after qlga_load_state + qlga_step) and store the checkpoints. */
+qlga_status qlga_adjoint_forward(qlga_handle* h, const void* x0_device, int64_t nsteps, int64_t checkpoint_every,
+                                 void* workspace, size_t workspace_bytes);
+
+/* cot_device (device, cotangent layout): dL/dx_n on entry, dL/dx_0 on exit, using the
+ * checkpoints of the preceding qlga_adjoint_forward() with the same nsteps and
+ * checkpoint_every.  Does not change the handle's state. */
+qlga_status qlga_adjoint_backward(qlga_handle* h, int64_t nsteps, int64_t checkpoint_every, void* workspace,
+                                  size_t workspace_bytes, void* cot_device, double* dcoup);
+
+/* qlga_adjoint_forward followed by qlga_adjoint_backward. */
+qlga_status qlga_adjoint_run(qlga_handle* h, const void* x0_device, int64_t nsteps, int64_t checkpoint_every,
+                             void* workspace, size_t workspace_bytes, void* cot_device, double* dcoup);
+
+/* One step pulled back at the state x_device (device, state layout): cot_device holds
+ * dL/dx_{k+1} on entry and dL/dx_k on exit.  Workspace as for nsteps = 1,
+ * checkpoint_every = 1.  Does not change the handle's state. */
+qlga_status qlga_adjoint_step(qlga_handle* h, const void* x_device, void* cot_device, void* workspace,
+                              size_t workspace_bytes, double* dcoup);
+
+/* ---------------------------------------------------------------------------------------
  * Batches: many independent periodic 1D lattices of uneven length, each with its own
  * couplings, advanced together (one fused pass over all of them per step).  The state buffer of
  * a batch is the concatenation of the runs' 1D states, each in the layout above with ny = 1

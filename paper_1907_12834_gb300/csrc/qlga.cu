@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,7 @@
 #include "qlga_device.cuh"
 #include "qlga_step2d.cuh"
 #include "qlga_batch1d.cuh"
+#include "qlga_adjoint.cuh"
 
 #include <vector>
 
@@ -505,15 +507,15 @@ __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T*
 }
 
 
-// out[k] = compensated sum of partials[b][k] over blocks, in a fixed order: warp k reduces
-// quantity k, lane l takes blocks l, l+32, ..., then the 32 (sum, compensation) pairs combine
-// in a fixed butterfly.  Launch with OBS_COUNT warps.
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks,
+// out[k] = compensated sum of partials[b][k] over blocks (rows of ncols), in a fixed order: warp
+// k reduces quantity k, lane l takes blocks l, l+32, ..., then the 32 (sum, compensation) pairs
+// combine in a fixed butterfly.  Launch with ncols warps.
+__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, int ncols,
                                   double* __restrict__ out) {
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= OBS_COUNT) return;
+    if (k >= ncols) return;
     CompSum cs;
-    for (int b = lane; b < nblocks; b += 32) cs.add(partials[int64_t(b) * OBS_COUNT + k]);
+    for (int b = lane; b < nblocks; b += 32) cs.add(partials[int64_t(b) * ncols + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double os = __shfl_xor_sync(0xffffffffu, cs.s, o);
@@ -802,7 +804,7 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
                                                            cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
                                                            cfg->g2, scratch);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch (no-alloc)");
-    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, st>>>(scratch, blocks, result);
+    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, st>>>(scratch, blocks, OBS_COUNT, result);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (no-alloc)");
     double o[OBS_COUNT];
     QLGA_CUDA(cudaMemcpyAsync(o, result, sizeof(o), cudaMemcpyDeviceToHost, st), "no-alloc observables copy");
@@ -1040,7 +1042,7 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
         k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
                                                                   h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch");
-    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, h->stream>>>(h->partials, blocks, h->obs_dev);
+    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, h->stream>>>(h->partials, blocks, OBS_COUNT, h->obs_dev);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
     h->launches += 2;
     double o[OBS_COUNT];
@@ -1129,6 +1131,226 @@ const char* qlga_status_string(qlga_status s) {
 }
 
 const char* qlga_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ===================================================================== adjoint (reverse mode)
+//
+// Workspace of the adjoint calls, each part 256-byte aligned: the cotangent and a second
+// cotangent buffer (also the middle buffer of a two-pass 2D kinetic read-out), two buffers for
+// the post-potential states of a recomputed segment, the per-block coupling partials and their
+// sum, ceil(n / C) checkpoints (true states x_0, x_C, x_2C, ...) and C segment slots (true
+// states x_k of the segment being pulled back).  All state-sized parts use the resident layout.
+
+namespace {
+
+constexpr int kAdjMaxBlocks = 152 * 8;
+
+struct AdjLayout {
+    void* cot;
+    void* cot_tmp;
+    void* w1;
+    void* w2;
+    double* partials;
+    double* result;
+    char* ckpt;
+    char* slots;
+    size_t state;
+    int64_t nck, nslots;
+    size_t total;
+};
+
+AdjLayout adj_layout(const qlga_config& c, int64_t n, int64_t C, void* base) {
+    AdjLayout L{};
+    L.state = align256(state_bytes_of(c));
+    L.nck = n > 0 ? (n + C - 1) / C : 0;
+    L.nslots = n < C ? (n > 0 ? n : 1) : C;
+    char* p = static_cast<char*>(base);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* q = p ? p + off : nullptr;
+        off += align256(bytes);
+        return q;
+    };
+    L.cot = take(L.state);
+    L.cot_tmp = take(L.state);
+    L.w1 = take(L.state);
+    L.w2 = take(L.state);
+    L.partials = reinterpret_cast<double*>(take(sizeof(double) * 3 * kAdjMaxBlocks));
+    L.result = reinterpret_cast<double*>(take(sizeof(double) * 3));
+    L.ckpt = take(L.state * size_t(L.nck));
+    L.slots = take(L.state * size_t(L.nslots));
+    L.total = off;
+    return L;
+}
+
+qlga_status adj_check(qlga_handle* h, int64_t n, int64_t C, void* ws, size_t ws_bytes, AdjLayout* L) {
+    if (!h || !ws) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (h->cfg.interleave) return fail(QLGA_ERR_UNSUPPORTED, "the adjoint covers the plain step only (interleave = 0)%s");
+    if (n < 0 || C < 1) return fail(QLGA_ERR_INVALID_ARG, "nsteps must be >= 0 and checkpoint_every >= 1%s");
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return fail(QLGA_ERR_INVALID_ARG, "workspace must be 256-byte aligned%s");
+    *L = adj_layout(h->cfg, n, C, ws);
+    if (ws_bytes < L->total) return fail(QLGA_ERR_INVALID_ARG, "adjoint workspace too small%s");
+    return QLGA_OK;
+}
+
+template <class T, int V, bool VJP>
+void adj_axis_t(qlga_handle* h, const void* gin, void* gout, const void* X, int axis, double* partials, int blocks) {
+    k_adjoint_axis<T, V, VJP><<<blocks, kAdjThreads, 0, h->stream>>>(
+        static_cast<const T*>(gin), static_cast<T*>(gout), static_cast<const T*>(X), h->cfg.nx, h->cfg.ny,
+        axis, AdjConst<T>(pot_params(h->cfg, 1.0)), partials, h->status);
+}
+
+template <class T, bool VJP>
+void adj_axis_v(qlga_handle* h, const void* gin, void* gout, const void* X, int axis, double* partials, int blocks) {
+    if (h->cfg.kinetic_variant == 0) adj_axis_t<T, 0, VJP>(h, gin, gout, X, axis, partials, blocks);
+    else adj_axis_t<T, 1, VJP>(h, gin, gout, X, axis, partials, blocks);
+}
+
+qlga_status adj_axis(qlga_handle* h, const void* gin, void* gout, const void* X, int axis, bool vjp, double* partials) {
+    const int blocks = grid_for_block(nsites_of(h->cfg), kAdjThreads, kAdjMaxBlocks);
+    if (h->cfg.precision == 32) {
+        if (vjp) adj_axis_v<float, true>(h, gin, gout, X, axis, partials, blocks);
+        else adj_axis_v<float, false>(h, gin, gout, X, axis, partials, blocks);
+    } else {
+        if (vjp) adj_axis_v<double, true>(h, gin, gout, X, axis, partials, blocks);
+        else adj_axis_v<double, false>(h, gin, gout, X, axis, partials, blocks);
+    }
+    QLGA_CUDA(cudaGetLastError(), "k_adjoint_axis launch");
+    h->launches += 1;
+    return QLGA_OK;
+}
+
+// cot <- (d step / d x at x_k)^T cot.  The cotangent lives in *cot; 1D swaps it with *tmp.
+qlga_status adj_pullback(qlga_handle* h, void** cot, void** tmp, const void* xk, double* partials) {
+    qlga_status s;
+    if (h->cfg.ndim == 1) {
+        s = adj_axis(h, *cot, *tmp, xk, 0, true, partials);
+        if (s != QLGA_OK) return s;
+        std::swap(*cot, *tmp);
+        return QLGA_OK;
+    }
+    // K = K_y K_x, so K^dagger = K_x^dagger K_y^dagger: y first, then x with the pull-back of U
+    s = adj_axis(h, *cot, *tmp, xk, 1, false, partials);
+    if (s != QLGA_OK) return s;
+    return adj_axis(h, *tmp, *cot, xk, 0, true, partials);
+}
+
+qlga_status adj_finish(qlga_handle* h, const AdjLayout& L, void* cot_res, void* cot_dev, double* dcoup) {
+    k_reduce_partials<<<1, 32 * 3, 0, h->stream>>>(L.partials, kAdjMaxBlocks, 3, L.result);
+    QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (adjoint)");
+    h->launches += 1;
+    qlga_status s = launch_convert(h, cot_res, cot_dev, false);
+    if (s != QLGA_OK) return s;
+    double d[3];
+    QLGA_CUDA(cudaMemcpyAsync(d, L.result, sizeof(d), cudaMemcpyDeviceToHost, h->stream), "adjoint result copy");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "adjoint sync");
+    if (dcoup)
+        for (int i = 0; i < 3; ++i) dcoup[i] = d[i];
+    return check_status_word(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+qlga_status qlga_adjoint_workspace_bytes(const qlga_config* cfg, int64_t nsteps, int64_t checkpoint_every,
+                                         size_t* bytes) {
+    qlga_status s = check_cfg(cfg);
+    if (s != QLGA_OK) return s;
+    if (!bytes) return fail(QLGA_ERR_INVALID_ARG, "bytes is NULL%s");
+    if (nsteps < 0 || checkpoint_every < 1) return fail(QLGA_ERR_INVALID_ARG, "nsteps must be >= 0 and checkpoint_every >= 1%s");
+    *bytes = adj_layout(*cfg, nsteps, checkpoint_every, nullptr).total;
+    return QLGA_OK;
+}
+
+qlga_status qlga_adjoint_step(qlga_handle* h, const void* x_device, void* cot_device, void* workspace,
+                              size_t workspace_bytes, double* dcoup) {
+    AdjLayout L;
+    qlga_status s = adj_check(h, 1, 1, workspace, workspace_bytes, &L);
+    if (s != QLGA_OK) return s;
+    if (!x_device || !cot_device) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    s = launch_convert(h, x_device, L.slots, true);
+    if (s != QLGA_OK) return s;
+    s = launch_convert(h, cot_device, L.cot, true);
+    if (s != QLGA_OK) return s;
+    QLGA_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(double) * 3 * kAdjMaxBlocks, h->stream), "partials clear");
+    void *cot = L.cot, *tmp = L.cot_tmp;
+    s = adj_pullback(h, &cot, &tmp, L.slots, L.partials);
+    if (s != QLGA_OK) return s;
+    return adj_finish(h, L, cot, cot_device, dcoup);
+}
+
+qlga_status qlga_adjoint_forward(qlga_handle* h, const void* x0_device, int64_t nsteps, int64_t checkpoint_every,
+                                 void* workspace, size_t workspace_bytes) {
+    AdjLayout L;
+    qlga_status s = adj_check(h, nsteps, checkpoint_every, workspace, workspace_bytes, &L);
+    if (s != QLGA_OK) return s;
+    if (!x0_device) return fail(QLGA_ERR_INVALID_ARG, "x0 is NULL%s");
+    s = qlga_load_state(h, x0_device, QLGA_DEVICE);
+    if (s != QLGA_OK) return s;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        if (k % checkpoint_every == 0) {
+            const void* view = nullptr;
+            s = true_state_view(h, &view);
+            if (s != QLGA_OK) return s;
+            QLGA_CUDA(cudaMemcpyAsync(L.ckpt + L.state * size_t(k / checkpoint_every), view,
+                                      state_bytes_of(h->cfg), cudaMemcpyDeviceToDevice, h->stream),
+                      "checkpoint copy");
+        }
+        s = qlga_step(h, 1);
+        if (s != QLGA_OK) return s;
+    }
+    return QLGA_OK;
+}
+
+qlga_status qlga_adjoint_backward(qlga_handle* h, int64_t nsteps, int64_t checkpoint_every, void* workspace,
+                                  size_t workspace_bytes, void* cot_device, double* dcoup) {
+    AdjLayout L;
+    qlga_status s = adj_check(h, nsteps, checkpoint_every, workspace, workspace_bytes, &L);
+    if (s != QLGA_OK) return s;
+    if (!cot_device) return fail(QLGA_ERR_INVALID_ARG, "cot is NULL%s");
+    const size_t nb = state_bytes_of(h->cfg);
+    s = launch_convert(h, cot_device, L.cot, true);
+    if (s != QLGA_OK) return s;
+    QLGA_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(double) * 3 * kAdjMaxBlocks, h->stream), "partials clear");
+    void *cot = L.cot, *tmp = L.cot_tmp;
+    for (int64_t j = L.nck - 1; j >= 0; --j) {
+        const int64_t start = j * checkpoint_every;
+        const int64_t len = std::min(nsteps - start, checkpoint_every);
+        // recompute x_start .. x_{start+len-1} into the slots from the checkpoint:
+        // y = U x (post-potential), x_next = K y, y_next = U K y (one fused launch)
+        char* slot0 = L.slots;
+        QLGA_CUDA(cudaMemcpyAsync(slot0, L.ckpt + L.state * size_t(j), nb, cudaMemcpyDeviceToDevice, h->stream), "slot copy");
+        if (len > 1) {
+            void *y = L.w1, *y2 = L.w2;
+            QLGA_CUDA(cudaMemcpyAsync(y, slot0, nb, cudaMemcpyDeviceToDevice, h->stream), "segment copy");
+            s = launch_pot(h, y, 1.0);
+            if (s != QLGA_OK) return s;
+            for (int64_t i = 1; i < len; ++i) {
+                s = kinetic_into(h, y, L.slots + L.state * size_t(i), tmp, false);
+                if (s != QLGA_OK) return s;
+                if (i + 1 < len) {
+                    s = kinetic_into(h, y, y2, tmp, true);
+                    if (s != QLGA_OK) return s;
+                    std::swap(y, y2);
+                }
+            }
+        }
+        for (int64_t i = len - 1; i >= 0; --i) {
+            s = adj_pullback(h, &cot, &tmp, L.slots + L.state * size_t(i), L.partials);
+            if (s != QLGA_OK) return s;
+        }
+    }
+    return adj_finish(h, L, cot, cot_device, dcoup);
+}
+
+qlga_status qlga_adjoint_run(qlga_handle* h, const void* x0_device, int64_t nsteps, int64_t checkpoint_every,
+                             void* workspace, size_t workspace_bytes, void* cot_device, double* dcoup) {
+    qlga_status s = qlga_adjoint_forward(h, x0_device, nsteps, checkpoint_every, workspace, workspace_bytes);
+    if (s != QLGA_OK) return s;
+    return qlga_adjoint_backward(h, nsteps, checkpoint_every, workspace, workspace_bytes, cot_device, dcoup);
+}
 
 }  // extern "C"
 

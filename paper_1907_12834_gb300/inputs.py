@@ -297,6 +297,62 @@ def config2(seed: int = 1909, n: int = 4096, eps: float = 0.1, steps: int = 5000
                     32 if dtype == np.float32 else 64, st, {"variant": variant})
 
 
+def config4(seed: int = 1911, n: int = 512, eps: float = 0.1, steps: int = 2000,
+            variant: str = "a", separation: float = 64.0, dtype=np.float32) -> Workload:
+    """2D vortex scattering on an n x n lattice (default 512^2), the adjoint workload: the
+    recipe of config2 at its own seed, with the vortex cores 64 sites apart as in config2 (at
+    separation n/64 = 8 sites the cores, about 10 sites across at eps = 0.1, would overlap)."""
+    w = config2(seed=seed, n=n, eps=eps, steps=steps, variant=variant, separation=separation, dtype=dtype)
+    w.meta["cores"] = dipole_cores(n, n, separation, variant)
+    return w
+
+
+def dipole_cores(nx: int, ny: int, separation: float, variant: str = "a"):
+    """(level index, x, y) of every vortex core of a config2 / config4 state."""
+    levels = {"a": (2, -2), "b": (1, -1), "c": (0,)}[variant]
+    cx, cy = nx / 2.0 + 0.5, ny / 2.0 + 0.5
+    out = []
+    for mf in levels:
+        for xc in (cx - separation / 2.0, cx + separation / 2.0):
+            out.append((2 - mf, xc, cy))
+    return out
+
+
+def kicked_state(psi, eps, cores, velocity, phase_levels=(), phases=None, sigma=16.0):
+    """Differentiable initial state (torch): the boson field psi (complex numpy [5, ny, nx])
+    with a windowed local kick at each vortex core and a relative phase on some levels.
+
+    Core j at (level l_j, x_j, y_j) gets psi_l <- psi_l exp(i v_j . d w_j), d the nearest-image
+    displacement from the core and w_j = exp(-|d|^2 / (2 sigma^2)): a local phase gradient v_j
+    (rad / site) that moves the core with a continuous velocity, unlike the quantised global
+    kicks 2 pi n / L.  Level phase_levels[k] is multiplied by exp(i phases[k]).
+    velocity: torch tensor [ncores, 2]; phases: torch tensor [len(phase_levels)].  Returns the
+    QLGA state a = b = eps psi / 2 as a torch tensor (5, ny, nx, 2, 2) of velocity's dtype and
+    device."""
+    import torch
+    dev, dt = velocity.device, velocity.dtype
+    ny, nx = psi.shape[1], psi.shape[2]
+    re = torch.tensor(np.ascontiguousarray(psi.real), dtype=dt, device=dev)
+    im = torch.tensor(np.ascontiguousarray(psi.imag), dtype=dt, device=dev)
+    x = torch.arange(nx, dtype=dt, device=dev)[None, :]
+    y = torch.arange(ny, dtype=dt, device=dev)[:, None]
+    theta = torch.zeros((5, ny, nx), dtype=dt, device=dev)
+    for j, (lev, xc, yc) in enumerate(cores):
+        dx = torch.remainder(x - xc + nx / 2.0, nx) - nx / 2.0
+        dy = torch.remainder(y - yc + ny / 2.0, ny) - ny / 2.0
+        w = torch.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma))
+        th = (velocity[j, 0] * dx + velocity[j, 1] * dy) * w
+        theta = theta + torch.nn.functional.one_hot(torch.tensor(lev), 5).to(dt).to(dev)[:, None, None] * th[None]
+    for k, lev in enumerate(phase_levels):
+        theta = theta + torch.nn.functional.one_hot(torch.tensor(lev), 5).to(dt).to(dev)[:, None, None] * phases[k]
+    c, s = torch.cos(theta), torch.sin(theta)
+    pr = re * c - im * s
+    pi = re * s + im * c
+    half = 0.5 * eps
+    a = torch.stack([half * pr, half * pi], dim=-1)
+    return torch.stack([a, a], dim=-2).contiguous()
+
+
 @dataclass
 class BatchWorkload:
     name: str

@@ -88,6 +88,13 @@ _SIGNATURES = {
                         ctypes.POINTER(ctypes.c_int64)],
     "qlga_batch_destroy": [_H],
     "qlga_destroy": [_H],
+    "qlga_adjoint_workspace_bytes": [_CFG, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
+    "qlga_adjoint_forward": [_H, _VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t],
+    "qlga_adjoint_backward": [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _VP,
+                              ctypes.POINTER(ctypes.c_double)],
+    "qlga_adjoint_run": [_H, _VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _VP,
+                         ctypes.POINTER(ctypes.c_double)],
+    "qlga_adjoint_step": [_H, _VP, _VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
 }
 
 
@@ -228,6 +235,44 @@ def qlga_destroy(h: int):
     _check(load_library().qlga_destroy(_H(h)), "qlga_destroy")
 
 
+def qlga_adjoint_workspace_bytes(cfg: QlgaConfig, nsteps: int, checkpoint_every: int) -> int:
+    out = ctypes.c_size_t()
+    _check(load_library().qlga_adjoint_workspace_bytes(ctypes.byref(cfg), ctypes.c_int64(int(nsteps)),
+                                                       ctypes.c_int64(int(checkpoint_every)),
+                                                       ctypes.byref(out)), "qlga_adjoint_workspace_bytes")
+    return out.value
+
+
+def qlga_adjoint_forward(h, x0_ptr, nsteps, checkpoint_every, ws_ptr, ws_bytes):
+    _check(load_library().qlga_adjoint_forward(_H(h), _VP(x0_ptr), ctypes.c_int64(int(nsteps)),
+                                               ctypes.c_int64(int(checkpoint_every)), _VP(ws_ptr),
+                                               ctypes.c_size_t(ws_bytes)), "qlga_adjoint_forward")
+
+
+def qlga_adjoint_backward(h, nsteps, checkpoint_every, ws_ptr, ws_bytes, cot_ptr) -> np.ndarray:
+    d = (ctypes.c_double * 3)()
+    _check(load_library().qlga_adjoint_backward(_H(h), ctypes.c_int64(int(nsteps)),
+                                                ctypes.c_int64(int(checkpoint_every)), _VP(ws_ptr),
+                                                ctypes.c_size_t(ws_bytes), _VP(cot_ptr), d),
+           "qlga_adjoint_backward")
+    return np.array(list(d))
+
+
+def qlga_adjoint_run(h, x0_ptr, nsteps, checkpoint_every, ws_ptr, ws_bytes, cot_ptr) -> np.ndarray:
+    d = (ctypes.c_double * 3)()
+    _check(load_library().qlga_adjoint_run(_H(h), _VP(x0_ptr), ctypes.c_int64(int(nsteps)),
+                                           ctypes.c_int64(int(checkpoint_every)), _VP(ws_ptr),
+                                           ctypes.c_size_t(ws_bytes), _VP(cot_ptr), d), "qlga_adjoint_run")
+    return np.array(list(d))
+
+
+def qlga_adjoint_step(h, x_ptr, cot_ptr, ws_ptr, ws_bytes) -> np.ndarray:
+    d = (ctypes.c_double * 3)()
+    _check(load_library().qlga_adjoint_step(_H(h), _VP(x_ptr), _VP(cot_ptr), _VP(ws_ptr),
+                                            ctypes.c_size_t(ws_bytes), d), "qlga_adjoint_step")
+    return np.array(list(d))
+
+
 def qlga_status_string(status: int) -> str:
     return load_library().qlga_status_string(int(status)).decode()
 
@@ -337,6 +382,46 @@ class Lattice:
         qlga_fields(self.handle, out.ctypes.data, QLGA_HOST)
         return out
 
+    # -- adjoint (reverse mode)
+    def adjoint_workspace(self, nsteps, checkpoint_every=100):
+        """Device workspace (torch uint8 tensor) for an adjoint run of nsteps; pass it to
+        adjoint_forward / adjoint_backward."""
+        nb = qlga_adjoint_workspace_bytes(self.cfg, nsteps, checkpoint_every)
+        return self._torch.empty(nb + 256, dtype=self._torch.uint8, device=self.device), nb
+
+    def _device_tensor(self, t):
+        assert isinstance(t, self._torch.Tensor) and t.is_cuda, "device tensor expected"
+        assert t.dtype == self.tdtype and tuple(t.shape) == self.shape, (t.dtype, t.shape)
+        return t.contiguous()
+
+    def adjoint_forward(self, x0, nsteps, checkpoint_every, ws):
+        """Load x0 (device tensor), run nsteps plain steps keeping checkpoints in ws."""
+        buf, nb = ws
+        x0 = self._device_tensor(x0)
+        qlga_adjoint_forward(self.handle, x0.data_ptr(), nsteps, checkpoint_every, self._aligned(buf), nb)
+
+    def adjoint_backward(self, cot, nsteps, checkpoint_every, ws):
+        """dL/dx_n (device tensor) -> (dL/dx_0 as a new tensor, dL/dg as numpy[3])."""
+        buf, nb = ws
+        c = self._device_tensor(cot).clone()
+        d = qlga_adjoint_backward(self.handle, nsteps, checkpoint_every, self._aligned(buf), nb, c.data_ptr())
+        return c, d
+
+    def adjoint_step(self, x, cot):
+        """Pull dL/dx_{k+1} back through one plain step at x (device tensors): returns
+        (dL/dx_k, dL/dg)."""
+        buf, nb = self.adjoint_workspace(1, 1)
+        x = self._device_tensor(x)
+        c = self._device_tensor(cot).clone()
+        d = qlga_adjoint_step(self.handle, x.data_ptr(), c.data_ptr(), self._aligned(buf), nb)
+        return c, d
+
+    def gradient(self, x0, nsteps, cot, checkpoint_every=100):
+        """dL/dx_0 and dL/dg for L with dL/dx_n = cot, through nsteps plain steps from x0."""
+        ws = self.adjoint_workspace(nsteps, checkpoint_every)
+        self.adjoint_forward(x0, nsteps, checkpoint_every, ws)
+        return self.adjoint_backward(cot, nsteps, checkpoint_every, ws)
+
     def synchronize(self):
         qlga_synchronize(self.handle)
 
@@ -359,6 +444,93 @@ class Lattice:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------------ autograd
+
+_lattice_cache = {}
+
+
+def _lattice_for(shape, dtype, g, kinetic_variant, device):
+    import torch
+    ny, nx = int(shape[1]), int(shape[2])
+    key = (ny, nx, dtype, tuple(float(v) for v in g), int(kinetic_variant), str(device))
+    lat = _lattice_cache.get(key)
+    if lat is None or lat.handle is None:
+        if len(_lattice_cache) > 8:
+            _lattice_cache.clear()
+        lat = Lattice(1 if ny == 1 else 2, nx, ny, 32 if dtype == torch.float32 else 64, g,
+                      kinetic_variant=kinetic_variant, device=device)
+        _lattice_cache[key] = lat
+    return lat
+
+
+def _make_evolve():
+    import torch
+
+    class Evolve(torch.autograd.Function):
+        """x_n = (K U)^n x_0 on the GPU, differentiable in x_0 and in the couplings g.
+
+        Forward: qlga_adjoint_forward (checkpoints every C steps, held with the function's
+        context).  Backward: qlga_adjoint_backward (segment recompute, pull-back)."""
+
+        @staticmethod
+        def forward(ctx, x0, g, nsteps, checkpoint_every, kinetic_variant):
+            lat = _lattice_for(x0.shape, x0.dtype, g.detach().cpu().tolist(), kinetic_variant, x0.device)
+            ws = lat.adjoint_workspace(nsteps, checkpoint_every)
+            lat.adjoint_forward(x0.detach(), nsteps, checkpoint_every, ws)
+            xn = lat.device_state()
+            ctx.lat, ctx.ws, ctx.nsteps, ctx.C = lat, ws, int(nsteps), int(checkpoint_every)
+            ctx.g_dtype, ctx.g_device = g.dtype, g.device
+            return xn
+
+        @staticmethod
+        def backward(ctx, grad_xn):
+            lat = ctx.lat
+            # the checkpoints stay with ctx: a graph kept with retain_graph may be pulled back again
+            cot, d = lat.adjoint_backward(grad_xn.to(lat.tdtype).contiguous(), ctx.nsteps, ctx.C, ctx.ws)
+            dg = torch.tensor(d, dtype=ctx.g_dtype, device=ctx.g_device)
+            return cot, dg, None, None, None
+
+    return Evolve
+
+
+_evolve_fn = None
+
+
+def evolve(x0, g, nsteps, checkpoint_every=100, kinetic_variant=0):
+    """Differentiable run of nsteps plain QLGA steps.
+
+    x0: CUDA tensor (5, ny, nx, 2, 2), float64 or float32 (the run's precision); ny = 1 is 1D.
+    g: tensor of the couplings (g0, g1, g2).  Returns x_n; gradients flow to x0 and g through the
+    library's adjoint (FP64 or FP32 like x0), with checkpoints every checkpoint_every steps."""
+    global _evolve_fn
+    if _evolve_fn is None:
+        _evolve_fn = _make_evolve()
+    return _evolve_fn.apply(x0, g, int(nsteps), int(checkpoint_every), int(kinetic_variant))
+
+
+def population(x, level):
+    """Objective: qubit-basis population sum |a_m|^2 + |b_m|^2 of level index `level`
+    (0..4 for m = +2..-2) of a state tensor (5, ny, nx, 2, 2)."""
+    return (x[level] * x[level]).sum()
+
+
+def singlet_fraction(x):
+    """Objective: sum |psi^T J psi|^2 / sum rho^2 of the boson field psi = a + b of a state
+    tensor (5, ny, nx, 2, 2), J with (J psi)_m = (-1)^m psi_{-m}."""
+    pr = x[:, :, :, 0, 0] + x[:, :, :, 1, 0]
+    pi = x[:, :, :, 0, 1] + x[:, :, :, 1, 1]
+    rho = (pr * pr + pi * pi).sum(0)
+    # theta = sum_m (-1)^m psi_m psi_{-m} = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2
+    def prod(i, j):
+        return pr[i] * pr[j] - pi[i] * pi[j], pr[i] * pi[j] + pi[i] * pr[j]
+    r20, i20 = prod(0, 4)
+    r11, i11 = prod(1, 3)
+    r00, i00 = prod(2, 2)
+    tr = 2 * r20 - 2 * r11 + r00
+    ti = 2 * i20 - 2 * i11 + i00
+    return (tr * tr + ti * ti).sum() / (rho * rho).sum()
 
 
 # ------------------------------------------------------------------ batches of 1D lattices

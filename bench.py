@@ -57,6 +57,26 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_seed(rank):
+    """Each rank advances its own independent lattice: config 2's seed offset by the rank."""
+    return 1909 + rank
+
+
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, sites, steps, seconds):
+    """Whole-job rate: the site-updates of all ranks over the slowest rank's time."""
+    return world * sites * steps / seconds
+
+
 # ----------------------------------------------------------------------------- helpers
 
 class ClockSampler:
@@ -180,7 +200,7 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
-    w = inputs.config2(seed=1909 + rank, n=n)
+    w = inputs.config2(seed=replica_seed(rank), n=n)
     lat = qlga.Lattice(2, n, n, precision=32, g=w.g, epsilon=w.eps)
     stream = lat.stream
     sites = n * n
@@ -222,19 +242,12 @@ def run_gb300(args):
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     plain = [t for i, t in enumerate(step_ms) if i not in obs_steps] or step_ms
     kernel_ms = statistics.mean(plain)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(lat, settled, args, torch, qlga, sites)
-        if dist:
-            t = torch.tensor([e2e["seconds"]], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * sites * args.steps / float(t.item())
-        e2e.pop("seconds")
+        e2e["value"] = job_rate(world, sites, args.steps, max_over_ranks(e2e.pop("seconds"), dist, "cuda"))
     lat.close()
 
     if rank != 0:
@@ -245,7 +258,7 @@ def run_gb300(args):
     achieved = BYTES_PER_SITE_F32 * sites / (kernel_ms * 1e-3) / 1e9
     traffic = recorded_traffic(n)
     line = {
-        "metric": METRIC, "value": world * sites * args.steps / (elapsed_ms * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": job_rate(world, sites, args.steps, elapsed_ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Pade vortex dipoles)",

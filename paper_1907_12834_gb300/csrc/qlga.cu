@@ -5,7 +5,6 @@
 // reporting) and the generic kernels:
 //   k_potential      U = exp(-i delta V(psi)) on every site, in place            (Sec. VII.B)
 //   k_kinetic_axis   one axis of the kinetic operator, optionally followed by U  (Sec. VII.B)
-//   k_block          one kinetic block I'_c (interleaved step)                   (Sec. VII.B)
 //   k_observables    FP64 sums of Sec. IV.A / IV.C, two-level deterministic reduction
 // The fused 2D FP32 step (one HBM read and one write of the state per step) is in
 // qlga_step2d.cuh.
@@ -31,6 +30,7 @@
 #include "qlga_step2d.cuh"
 #include "qlga_batch1d.cuh"
 #include "qlga_adjoint.cuh"
+#include "qlga_interleave.cuh"
 
 #include <vector>
 
@@ -188,65 +188,6 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
         }
         if (POT) potential_site<T, std::is_same<T, float>::value>(oa, ob, PC, T(1), T(0.5), status);
         if (active) SiteIO<T>::store(out, nsites, site, oa, ob);
-    }
-}
-
-// One kinetic block I'_q = S_q C' S^T_q C along `axis` (out of place): the interleaved step
-// applies U^(1/4) or U^(1/8) between blocks.  out_q(j) = W_q(j-1), out_o(j) = W_o(j) with
-// W = C' Z, Z_q(j) = Y_q(j+1), Z_o(j) = Y_o(j), Y = C in.
-template <class T, int VARIANT>
-__global__ void __launch_bounds__(kThreads) k_block(const T* __restrict__ in, T* __restrict__ out,
-                                                    int64_t nx, int64_t ny, int axis, int q) {
-    const int64_t nsites = nx * ny;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    // collides in the (a, b) basis: C1 = 1/2[[1-i, 1+i], [1+i, 1-i]], C2 = 1/2[[1+i, 1-i], [1-i, 1+i]]
-    const cpx<T> p = {T(0.5), T(-0.5)}, mq = {T(0.5), T(0.5)};  // (1-i)/2, (1+i)/2
-    for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
-        const int64_t x = site % nx, y = site / nx;
-        int64_t nbs[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (axis == 0) {
-                int64_t xx = x + k - 1;
-                xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
-                nbs[k] = y * nx + xx;
-            } else {
-                int64_t yy = y + k - 1;
-                yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-                nbs[k] = yy * nx + x;
-            }
-        }
-        cpx<T> oa[5], ob[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            cpx<T> Y[3][2];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                cpx<T> a, b;
-                load_pair<T>(in, nsites, m, nbs[k], a, b);
-                // first collide: K1 uses C1, K2 uses C2 (= C1 with the roles of p, mq swapped)
-                const cpx<T> d0 = VARIANT == 0 ? p : mq, o0 = VARIANT == 0 ? mq : p;
-                Y[k][0] = cmul(d0, a) + cmul(o0, b);
-                Y[k][1] = cmul(o0, a) + cmul(d0, b);
-            }
-            // W at j-1 (k = 0) and j (k = 1)
-            cpx<T> W[2][2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                cpx<T> Z[2];
-                Z[q] = Y[k + 1][q];
-                Z[1 - q] = Y[k][1 - q];
-                // second collide: C1 for both variants (C2^dagger = C1)
-                W[k][0] = cmul(p, Z[0]) + cmul(mq, Z[1]);
-                W[k][1] = cmul(mq, Z[0]) + cmul(p, Z[1]);
-            }
-            cpx<T> o[2];
-            o[q] = W[0][q];
-            o[1 - q] = W[1][1 - q];
-            oa[m] = o[0];
-            ob[m] = o[1];
-        }
-        SiteIO<T>::store(out, nsites, site, oa, ob);
     }
 }
 
@@ -645,22 +586,33 @@ qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
     return h->cfg.precision == 32 ? launch_potential<float>(h, buf, delta) : launch_potential<double>(h, buf, delta);
 }
 
-qlga_status launch_block(qlga_handle* h, const void* in, void* out, int axis, int q) {
-    const int64_t n = nsites_of(h->cfg);
-    const int nt = block_for(n);
-    const int g = grid_for_block(n, nt);
-    if (h->cfg.precision == 32) {
-        if (h->cfg.kinetic_variant == 0)
-            k_block<float, 0><<<g, nt, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
-        else
-            k_block<float, 1><<<g, nt, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+// One interleaved axis pass (U^(1/(4 ndim)) before each of the axis's four blocks), in -> out.
+template <class T, int V>
+void interleave_launch_t(qlga_handle* h, const void* in, void* out, int axis) {
+    const PotConst<T> PC(pot_params(h->cfg, 1.0 / (4.0 * h->cfg.ndim)));
+    const int64_t nx = h->cfg.nx, ny = h->cfg.ny;
+    if (axis == 0) {
+        const int64_t tiles = ((nx + kIlvXTile - 1) / kIlvXTile) * ny;
+        const int grid = int(tiles < 152 * 16 ? tiles : 152 * 16);
+        k_interleave_x<T, V><<<grid, kIlvXThreads, 0, h->stream>>>(static_cast<const T*>(in), static_cast<T*>(out), nx, ny, PC, h->status);
     } else {
-        if (h->cfg.kinetic_variant == 0)
-            k_block<double, 0><<<g, nt, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
-        else
-            k_block<double, 1><<<g, nt, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny, axis, q);
+        const int64_t strips = (nx + kIlvYThreads - 1) / kIlvYThreads;
+        int64_t chunks = (152 * 8) / strips;
+        chunks = chunks < 1 ? 1 : (chunks > ny ? ny : chunks);
+        k_interleave_y<T, V><<<int(strips * chunks), kIlvYThreads, 0, h->stream>>>(static_cast<const T*>(in), static_cast<T*>(out), nx, ny, int(chunks), PC, h->status);
     }
-    QLGA_CUDA(cudaGetLastError(), "k_block launch");
+}
+
+qlga_status launch_interleave(qlga_handle* h, const void* in, void* out, int axis) {
+    const bool f = h->cfg.precision == 32;
+    if (h->cfg.kinetic_variant == 0) {
+        if (f) interleave_launch_t<float, 0>(h, in, out, axis);
+        else interleave_launch_t<double, 0>(h, in, out, axis);
+    } else {
+        if (f) interleave_launch_t<float, 1>(h, in, out, axis);
+        else interleave_launch_t<double, 1>(h, in, out, axis);
+    }
+    QLGA_CUDA(cudaGetLastError(), "interleave launch");
     h->launches += 1;
     return QLGA_OK;
 }
@@ -983,19 +935,15 @@ qlga_status qlga_step(qlga_handle* h, int64_t n) {
     qlga_status s = QLGA_OK;
     for (int64_t i = 0; i < n; ++i) {
         if (h->cfg.interleave) {
-            // U^(1/(4 ndim)) before every kinetic block, blocks I'_2 I'_2 I'_1 I'_1 per axis
+            // U^(1/(4 ndim)) before every kinetic block, blocks I'_2 I'_2 I'_1 I'_1 per axis:
+            // one fused pass per axis
             s = materialize(h);
             if (s != QLGA_OK) return s;
-            const double frac = 1.0 / (4.0 * h->cfg.ndim);
-            static const int qs[4] = {1, 1, 0, 0};
-            for (int axis = 0; axis < h->cfg.ndim; ++axis)
-                for (int k = 0; k < 4; ++k) {
-                    s = launch_pot(h, h->X[h->cur], frac);
-                    if (s != QLGA_OK) return s;
-                    s = launch_block(h, h->X[h->cur], h->X[1 - h->cur], axis, qs[k]);
-                    if (s != QLGA_OK) return s;
-                    h->cur ^= 1;
-                }
+            for (int axis = 0; axis < h->cfg.ndim; ++axis) {
+                s = launch_interleave(h, h->X[h->cur], h->X[1 - h->cur], axis);
+                if (s != QLGA_OK) return s;
+                h->cur ^= 1;
+            }
         } else if (!h->pending_k) {
             s = launch_pot(h, h->X[h->cur], 1.0);  // X = U psi, true state K X
             if (s != QLGA_OK) return s;

@@ -122,16 +122,19 @@ def test_steps_fp32_fused_2d(nx, ny, variant):
     assert rel_l2(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("ndim,nx,ny", [(1, 64, 1), (2, 24, 20)])
+@pytest.mark.parametrize("ndim,nx,ny,variant", [(1, 64, 1, 0), (2, 24, 20, 0), (1, 131, 1, 1),
+                                                 (2, 130, 37, 1), (2, 250, 9, 0), (1, 8, 1, 0)])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_interleaved_steps(ndim, nx, ny, precision):
-    rng = np.random.default_rng(29)
+def test_interleaved_steps(ndim, nx, ny, variant, precision):
+    """Fused interleaved passes (x tiles of 120 sites with ragged tails, y row chunks) against the
+    oracle's operator-by-operator interleaved step."""
+    rng = np.random.default_rng(29 + nx)
     st = I.random_state(rng, nx, ny, scale=0.05)
     if precision == 32:
         st = st.astype(np.float32)
     g = G_SETS[1]
-    got = run_gpu(st, ndim, nx, ny, g, 6, precision, interleave=1)
-    ref = run_oracle(st, ndim, nx, ny, g, 6, interleave=1)
+    got = run_gpu(st, ndim, nx, ny, g, 6, precision, interleave=1, variant=variant)
+    ref = run_oracle(st, ndim, nx, ny, g, 6, interleave=1, variant=variant)
     assert rel_l2(got, ref) <= (1e-11 if precision == 64 else 1e-5)
 
 

@@ -10,7 +10,7 @@
 //
 // Potential step at one site (a' = U a, b' = U b, U = exp(-i delta V(psi)), psi = a + b):
 //   gbar_a = U^dagger gbar_a' + h,   gbar_b = U^dagger gbar_b' + h,
-// with h the gradient through psi.  Writing V = c 1 + W (c = (g0 + g2/25) rho) and B = -i delta W,
+// with h the gradient through psi.  Writing V = c 1 + W (c = (g0 + g2/10) rho) and B = -i delta W,
 // U = e^{-i delta c} P(B) with P the Taylor polynomial of the forward step.  With
 // M = a gbar_a'^dagger + b gbar_b'^dagger and the Frechet derivative L(B, E) = d/dt P(B + t E):
 //   tau    = Im tr(U M) = Im sum_r gbar_r^dagger U x_r                        (r = a, b)

@@ -193,10 +193,11 @@ __device__ __forceinline__ void kinetic_axis_site(const cpx<T> (*nba)[5], const 
 // side of Eq. eomspin2 written as V(psi) psi):
 //     V = g0 rho 1 + g1 (F_x f_x + F_y f_y + F_z f_z) + (g2/5) s s^dagger,
 //     F_nu = psi^dagger f_nu psi,  s_m = (-1)^m conj(psi_{-m}).
-// Evaluation: V = c 1 + W with c = (g0 + g2/25) rho its mean eigenvalue, so
+// Evaluation: V = c 1 + W with c = (g0 + g2/10) rho, the centre of V's spectral bounds, so
 // U = e^{-i delta c} exp(-i delta W).  W is tridiagonal (the spin term: f_+ = f_x + i f_y has
 // entries 2, 2 sqrt(3/2), 2 sqrt(3/2), 2 above the diagonal) plus the rank-one singlet term, and
-// ||delta W|| <= beta = delta (2 |g1| |F| + (4/25) |g2| rho).  exp(-i delta W) is applied to the
+// ||delta W|| <= beta = delta (2 |g1| |F| + |g2| rho / 10) (the spin term has eigenvalues
+// g1 |F| m, m = -2..2; the singlet term (g2/5) s s^dagger has eigenvalues g2 rho / 5 and 0).  exp(-i delta W) is applied to the
 // vectors psi and d = a - b by its Taylor polynomial (Horner form) of the smallest degree K
 // with beta^(K+1)/(K+1)! <= tol; then a = U(psi + d)/2, b = U(psi - d)/2.  K is made uniform
 // across the warp, so the loop never diverges.
@@ -214,22 +215,22 @@ struct PotParams {
 // Constants of the potential in the arithmetic type, computed on the host from PotParams.
 template <class T>
 struct PotConst {
-    T cphase;  // delta (g0 + g2/25): e^{-i delta c} with c = (g0 + g2/25) rho
+    T cphase;  // delta (g0 + g2/10): e^{-i delta c} with c = (g0 + g2/10) rho
     T dz;      // delta g1: diagonal spin entry per unit F_z m
-    T dr;      // delta g2 / 25: diagonal shift of the singlet term per unit rho
+    T dr;      // delta g2 / 10: diagonal shift of the singlet term per unit rho
     T e0, e1;  // delta g1, delta g1 sqrt(3/2): off-diagonal spin entries per unit F_+
     T R;       // delta g2 / 5: singlet rank-one term
-    T b1, b2;  // 2 |g1| delta, (4/25) |g2| delta: beta = b1 |F| + b2 rho
+    T b1, b2;  // 2 |g1| delta, |g2| delta / 10: beta = b1 |F| + b2 rho
     PotConst() = default;
     __host__ __device__ explicit PotConst(const PotParams& P) {
-        cphase = T(P.delta * (P.g0 + P.g2 / 25.0));
+        cphase = T(P.delta * (P.g0 + P.g2 / 10.0));
         dz = T(P.delta * P.g1);
-        dr = T(P.delta * P.g2 / 25.0);
+        dr = T(P.delta * P.g2 / 10.0);
         e0 = T(P.delta * P.g1);
         e1 = T(P.delta * P.g1 * 1.2247448713915890491);  // sqrt(3/2)
         R = T(P.delta * P.g2 / 5.0);
         b1 = T(2.0 * fabs(P.g1) * P.delta);
-        b2 = T(0.16 * fabs(P.g2) * P.delta);
+        b2 = T(0.1 * fabs(P.g2) * P.delta);
     }
 };
 

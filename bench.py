@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-paths", action="store_true",
+                   help="skip the FP64 / batched / adjoint / interleaved comparison runs")
     return p.parse_args()
 
 
@@ -276,11 +278,115 @@ def run_gb300(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if not args.no_paths:
+        line["paths"] = run_paths(args, torch, qlga, inputs, w.state, line["value"] / world)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w.state, w.g, args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _timed_steps(torch, lat, steps):
+    """Device time per step of `steps` plain steps on the lattice's stream (after a warm-up)."""
+    lat.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step(steps)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / steps
+
+
+def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
+    """The comparisons the metric names, each timed on the device after a warm-up: the plain
+    step in FP64 on the same lattice, the batched 1D path against one FP64 run at a time, the
+    adjoint (checkpointed forward + pull-back) against the plain FP64 step on its lattice, and the
+    interleaved step.  Accuracy of each path against the FP64 oracle is established by the
+    parity tests (FP64 1e-11, FP32 1e-5 per configuration)."""
+    import numpy as np
+    out = {}
+    n = args.n
+    # plain FP64 on the bench lattice (same initial data)
+    lat = qlga.Lattice(2, n, n, precision=64, g=inputs.CONFIG2_G)
+    lat.load_state(state_f32.astype(np.float64))
+    sec = _timed_steps(torch, lat, 3)
+    lat.close()
+    out["plain_fp64_2d"] = {"lattice": [n, n], "site_updates_per_s": n * n / sec, "ms_per_step": sec * 1e3}
+    out["fp32_over_fp64_2d"] = rate_fp32 / out["plain_fp64_2d"]["site_updates_per_s"]
+    # interleaved FP32 on the bench lattice
+    lat = qlga.Lattice(2, n, n, precision=32, g=inputs.CONFIG2_G, interleave=1)
+    lat.load_state(state_f32)
+    sec = _timed_steps(torch, lat, 10)
+    lat.close()
+    out["interleaved_fp32_2d"] = {"lattice": [n, n], "site_updates_per_s": n * n / sec, "ms_per_step": sec * 1e3}
+    # batched 1D (256 runs, FP32, graph replay) against one FP64 run of the mean length
+    bw = inputs.config3()
+    b = qlga.Batch1D(bw.lengths, bw.couplings, precision=32)
+    b.load_state(bw.state)
+    b.step(20)                                   # tuner + graph capture
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(200)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3 / 200
+    total = int(bw.lengths.sum())
+    info = b.info()
+    b.close()
+    L = int(round(float(bw.lengths.mean())))
+    rng = np.random.default_rng(1910)
+    one = inputs.boson_to_state(inputs.scattering_run(rng, L, bw.eps), bw.eps)
+    lat = qlga.Lattice(1, L, 1, precision=64, g=tuple(bw.couplings[0]))
+    lat.load_state(one)
+    sec1 = _timed_steps(torch, lat, 200)
+    lat.close()
+    out["batched_fp32_1d"] = {"runs": int(len(bw.lengths)), "sites": total, "site_updates_per_s": total / sec,
+                              "ms_per_step": sec * 1e3, "tile_width": info["tile_width"]}
+    out["single_run_fp64_1d"] = {"lattice": L, "site_updates_per_s": L / sec1, "ms_per_step": sec1 * 1e3}
+    out["batched_fp32_over_single_run_fp64"] = (total / sec) / (L / sec1)
+    # adjoint on the 512^2 lattice: 200 steps forward with checkpoints every 100, then the pull-back
+    for prec in (32, 64):
+        w4 = inputs.config4(dtype=np.float32 if prec == 32 else np.float64)
+        dt = torch.float32 if prec == 32 else torch.float64
+        x0 = torch.tensor(w4.state, dtype=dt, device="cuda")
+        lat = qlga.Lattice(2, 512, 512, precision=prec, g=w4.g)
+        steps, C = 200, 100
+        ws = lat.adjoint_workspace(steps, C)
+        lat.adjoint_forward(x0, steps, C, ws)        # warm-up
+        lat.adjoint_backward(x0, steps, C, ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.adjoint_forward(x0, steps, C, ws)
+        xn = lat.device_state()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        cot, _ = lat.adjoint_backward(xn, steps, C, ws)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        err = float(torch.linalg.vector_norm((cot - x0).double()) / torch.linalg.vector_norm(x0.double()))
+        plain = None
+        if prec == 64:
+            lat.load_state(x0)
+            plain = 512 * 512 / _timed_steps(torch, lat, 10)
+        lat.close()
+        del ws
+        sites = 512 * 512
+        out["adjoint_fp%d_2d_512" % prec] = {
+            "steps": steps, "checkpoint_every": C,
+            "gradient_site_steps_per_s": sites * steps / (t2 - t0),
+            "forward_ms_per_step": (t1 - t0) * 1e3 / steps, "backward_ms_per_step": (t2 - t1) * 1e3 / steps,
+            "norm_identity_error": err}
+        if plain:
+            out["plain_fp64_2d_512"] = {"site_updates_per_s": plain}
+    out["adjoint_fp32_over_plain_fp64_2d_512"] = (out["adjoint_fp32_2d_512"]["gradient_site_steps_per_s"] /
+                                                 out["plain_fp64_2d_512"]["site_updates_per_s"])
+    out["note"] = ("rates on the device with CUDA events (adjoint: wall time of the two calls, host "
+                   "synchronised); gradient_site_steps_per_s counts sites x steps of a full gradient "
+                   "(forward with checkpoints + recompute + pull-back); norm_identity_error = "
+                   "|dL/dx0 - x0| / |x0| for L = |x_n|^2 / 2")
+    return out
 
 
 def run_e2e(lat, state, args, torch, qlga, sites):

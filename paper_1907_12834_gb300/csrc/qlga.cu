@@ -478,6 +478,73 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
 
 }  // namespace qlga
 
+// ===================================================================== fused 2D step: launch
+
+namespace qlga {
+
+inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
+    return nx % kStep2dW == 0 && nx >= kStep2dW && ny >= 1 && nx <= (int64_t(1) << 30) &&
+           ny <= (int64_t(1) << 30);
+}
+
+// Chunks per strip so that the grid fills every SM once at the kernel's occupancy.
+inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
+    const int64_t strips = nx / kStep2dW;
+    int64_t chunks = (int64_t(sms) * per_sm) / strips;
+    if (chunks < 1) chunks = 1;
+    if (chunks > ny) chunks = ny;
+    return int(chunks);
+}
+
+// Per-device launch facts (SM count, resident CTAs per SM), set up once per device.  The
+// shared-memory opt-in is a per-device function attribute, so it is applied on each device.
+struct Step2dDevice {
+    int sms = 0, per_sm = 0;
+};
+
+inline int step2d_device(Step2dDevice* out) {
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static Step2dDevice cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    Step2dDevice& d = cache[dev];
+    if (d.sms == 0) {
+        int sms = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step2d_f32<0, true>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
+        d.per_sm = per_sm > 0 ? per_sm : 1;
+        d.sms = sms;
+    }
+    *out = d;
+    return 0;
+}
+
+// Returns 0 on success (errors are left in cudaGetLastError()).  pot = false applies the kinetic
+// operator alone.
+inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant, bool pot,
+                             PotConst<float> PC, unsigned* status, cudaStream_t stream) {
+    Step2dDevice dv;
+    if (step2d_device(&dv)) return 1;
+    const int chunks = step2d_chunks(nx, ny, dv.sms, dv.per_sm);
+    const int grid = int(nx / kStep2dW) * chunks;
+    if (variant == 0) {
+        if (pot) k_step2d_f32<0, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<0, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    } else {
+        if (pot) k_step2d_f32<1, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<1, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    }
+    return cudaPeekAtLastError() != cudaSuccess;
+}
+
+}  // namespace qlga
+
 // ===================================================================== handle
 
 struct qlga_handle {

@@ -241,46 +241,5 @@ __global__ void __launch_bounds__(kStep2dW, 3)
     cp_async_wait<0>();
 }
 
-inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
-    return nx % kStep2dW == 0 && nx >= kStep2dW && ny >= 1 && nx <= (int64_t(1) << 30) &&
-           ny <= (int64_t(1) << 30);
-}
-
-// Chunks per strip so that the grid fills every SM once at the kernel's occupancy.
-inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
-    const int64_t strips = nx / kStep2dW;
-    int64_t chunks = (int64_t(sms) * per_sm) / strips;
-    if (chunks < 1) chunks = 1;
-    if (chunks > ny) chunks = ny;
-    return int(chunks);
-}
-
-// Returns 0 on success (errors are left in cudaGetLastError()).  pot = false applies the kinetic
-// operator alone.
-inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny, int variant, bool pot,
-                             PotConst<float> PC, unsigned* status, cudaStream_t stream) {
-    static int sms = 0, per_sm = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess) return 1;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step2d_f32<0, true>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
-    }
-    const int chunks = step2d_chunks(nx, ny, sms, per_sm > 0 ? per_sm : 1);
-    const int grid = int(nx / kStep2dW) * chunks;
-    if (variant == 0) {
-        if (pot) k_step2d_f32<0, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-        else k_step2d_f32<0, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-    } else {
-        if (pot) k_step2d_f32<1, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-        else k_step2d_f32<1, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-    }
-    return cudaPeekAtLastError() != cudaSuccess;
-}
-
 }  // namespace qlga
 

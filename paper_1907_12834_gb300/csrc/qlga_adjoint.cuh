@@ -236,10 +236,10 @@ __device__ __forceinline__ void frechet_rank2(const WOp<T>& W, const cpx<T> s[5]
 }
 
 // Pull-back through U at one site.  (a, b): the state before U.  (ga, gb): cotangents of the
-// outputs on entry, of the inputs on exit.  dc[3] += this site's dL/d(g0, g1, g2).
+// outputs on entry, of the inputs on exit.  dc[3] = this site's dL/d(g0, g1, g2).
 template <class T>
 __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<T> b[5], cpx<T> ga[5],
-                                                   cpx<T> gb[5], const AdjConst<T>& A, double dc[3],
+                                                   cpx<T> gb[5], const AdjConst<T>& A, T dc[3],
                                                    unsigned* status) {
     cpx<T> psi[5];
 #pragma unroll
@@ -302,9 +302,9 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
     cpx<T> sHs = {T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < 5; ++i) sHs = cfma(W.u[i], Hs[i], sHs);  // conj(s_i) = u_i
-    dc[0] += double(A.delta * rho * tau);
-    dc[1] += double(A.delta * (Fp.re * phx + Fp.im * phy + Fz * phz));
-    dc[2] += double(A.delta * sHs.re) / 5.0;
+    dc[0] = A.delta * rho * tau;
+    dc[1] = A.delta * (Fp.re * phx + Fp.im * phy + Fz * phz);
+    dc[2] = A.delta * sHs.re / T(5);
 
     // U^dagger on the incoming cotangents, plus h
     cpx<T> pa[5], pb[5];
@@ -331,6 +331,29 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
 // ------------------------------------------------------------------ kernel
 
 constexpr int kAdjThreads = 128;
+
+// Per-thread sum of the per-site coupling-gradient terms: FP64 for an FP64 state; compensated
+// (Kahan) FP32 for an FP32 state, whose terms carry FP32 rounding anyway and whose FP64 additions
+// would cost 64 FP32 slots each.  Block sums are FP64.
+template <class T>
+struct AdjSum;
+template <>
+struct AdjSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct AdjSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
 
 // Resident pair (a, bt) of level m at a site.
 template <class T>
@@ -360,7 +383,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_axis(const T* __restric
     constexpr KinStencil S = kStencilAdj[VARIANT];
     const int64_t nsites = nx * ny;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    double dsum[3] = {0.0, 0.0, 0.0};
+    AdjSum<T> dsum[3];
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
         const int64_t site = base + threadIdx.x;
         const bool active = site < nsites;
@@ -401,12 +424,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_axis(const T* __restric
         if (VJP) {
             cpx<T> a[5], b[5];
             SiteIO<T>::load(X, nsites, s, a, b);
-            double dc[3] = {0.0, 0.0, 0.0};
+            T dc[3];
             potential_vjp_site(a, b, ga, gb, A, dc, status);
             if (active) {
-                dsum[0] += dc[0];
-                dsum[1] += dc[1];
-                dsum[2] += dc[2];
+                dsum[0].add(dc[0]);
+                dsum[1].add(dc[1]);
+                dsum[2].add(dc[2]);
             }
         }
         if (active) SiteIO<T>::store(gout, nsites, site, ga, gb);
@@ -416,7 +439,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_axis(const T* __restric
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            double v = dsum[j];
+            double v = dsum[j].value();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) sh[wid][j] = v;

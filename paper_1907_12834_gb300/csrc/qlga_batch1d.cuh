@@ -72,14 +72,29 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
     const BatchTile tile = tiles[blockIdx.x];
     const BatchRun run = runs[tile.run];
     const int L = run.L;
-    for (int i = threadIdx.x; i < 5 * (W + 8); i += W) {
-        const int m = i / (W + 8), c = i - m * (W + 8);
-        int j = (tile.start - 4 + c) % L;
-        j = j < 0 ? j + L : j;
-        sm[m][c] = load_raw_pair(in, run.base + int64_t(m) * L + j);
+    const int t = threadIdx.x;
+    // staged column c holds site start - 4 + c of the run (periodic); thread t loads column 4 + t
+    // and threads 0..7 also one halo column (0..3, W+4..W+7).  All loads are issued before use.
+    auto wrap = [&](int j) {
+        if (L >= W + 8) return j < 0 ? j + L : (j >= L ? j - L : j);  // at most one wrap
+        j %= L;
+        return j < 0 ? j + L : j;
+    };
+    const int jm = wrap(tile.start + t);
+    const int ch = t < 4 ? t : W + t;
+    const int jh = wrap(tile.start - 4 + ch);
+    Pair4<T> vm[5], vh[5];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        vm[m] = load_raw_pair(in, run.base + int64_t(m) * L + jm);
+        if (t < 8) vh[m] = load_raw_pair(in, run.base + int64_t(m) * L + jh);
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        sm[m][4 + t] = vm[m];
+        if (t < 8) sm[m][ch] = vh[m];
     }
     __syncthreads();
-    const int t = threadIdx.x;
     const int j = tile.start + t;
     cpx<T> oa[5], ob[5];
 #pragma unroll

@@ -184,6 +184,12 @@ qlga_status qlga_fields(qlga_handle* h, void* dst, int where);
 qlga_status qlga_observables_noalloc(const qlga_config* cfg, const void* state_device,
                                      const void* ref_state_device, void* stream, qlga_obs* out);
 
+/* Steps per CUDA graph replay.  On lattices of at most 2^18 sites the step is bound by launch
+ * latency, so qlga_step() replays runs of `steps` fused steps (default 32) from a graph captured
+ * on first use (the same kernels with the same arguments; results are identical).  steps must be
+ * even, 0..4096; 0 turns graphs off.  Larger lattices start with 0. */
+qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps);
+
 /* Number of kernels this handle has launched since creation (a diagnostic for benchmarks). */
 qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count);
 

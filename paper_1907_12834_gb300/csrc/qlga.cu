@@ -40,6 +40,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kObsMaxBlocks = 152 * 8;
+constexpr int64_t kGraphMaxSites = int64_t(1) << 18;  // lattices replayed from step graphs
+constexpr int kGraphDefaultSteps = 32;
 
 thread_local std::string g_last_error;
 
@@ -560,6 +562,10 @@ struct qlga_handle {
     bool pending_k;  // buffer holds X with true state K X
     int64_t step;
     int64_t launches;  // kernels launched by this handle
+    // CUDA graphs of graph_steps fused steps starting (and ending) on buffer 0 or 1
+    int graph_steps;
+    int64_t graph_launches;  // kernels in one graph
+    cudaGraphExec_t graph[2];
 };
 
 namespace {
@@ -756,6 +762,55 @@ qlga_status check_status_word(qlga_handle* h) {
     return QLGA_OK;
 }
 
+// Capture (once per buffer parity) and launch a graph of graph_steps fused steps.  The graph
+// holds the same launches qlga_step issues one by one; graph_steps is even, so it starts and
+// ends on buffer h->cur.
+void graphs_release(qlga_handle* h) {
+    for (int p = 0; p < 2; ++p) {
+        if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
+        h->graph[p] = nullptr;
+    }
+}
+
+qlga_status graph_steps_launch(qlga_handle* h) {
+    cudaGraphExec_t& exec = h->graph[h->cur];
+    if (!exec) {
+        cudaStream_t cs = nullptr;
+        QLGA_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        cudaStream_t saved = h->stream;
+        const int64_t launches0 = h->launches;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        qlga_status s = QLGA_OK;
+        if (e == cudaSuccess) {
+            h->stream = cs;
+            int c = h->cur;
+            for (int k = 0; k < h->graph_steps && s == QLGA_OK; ++k) {
+                s = kinetic_into(h, h->X[c], h->X[1 - c], h->tmp, true);
+                c ^= 1;
+            }
+            h->stream = saved;
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        h->graph_launches = h->launches - launches0;
+        h->launches = launches0;
+        cudaStreamDestroy(cs);
+        if (s != QLGA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            exec = nullptr;
+            return cuda_fail(e, "step graph capture");
+        }
+    }
+    QLGA_CUDA(cudaGraphLaunch(exec, h->stream), "step graph launch");
+    h->launches += h->graph_launches;
+    return QLGA_OK;
+}
+
 }  // namespace
 
 // ===================================================================== allocation-free observables
@@ -885,6 +940,10 @@ static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* str
     h->pending_k = false;
     h->step = 0;
     h->launches = 0;
+    // small lattices are bound by launch latency: replay runs of fused steps from a graph
+    h->graph_steps = nsites_of(*cfg) <= kGraphMaxSites ? kGraphDefaultSteps : 0;
+    h->graph_launches = 0;
+    h->graph[0] = h->graph[1] = nullptr;
     QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
     QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
     return QLGA_OK;
@@ -1001,6 +1060,16 @@ qlga_status qlga_step(qlga_handle* h, int64_t n) {
     if (n < 0) return fail(QLGA_ERR_INVALID_ARG, "n must be >= 0%s");
     qlga_status s = QLGA_OK;
     for (int64_t i = 0; i < n; ++i) {
+        // runs of fused steps on a small lattice replay a captured graph (same kernels, same
+        // arguments, one graph launch instead of graph_steps stream launches)
+        if (!h->cfg.interleave && h->pending_k && h->graph_steps > 0 && n - i >= h->graph_steps &&
+            h->step >= 2) {
+            s = graph_steps_launch(h);
+            if (s != QLGA_OK) return s;
+            h->step += h->graph_steps;
+            i += h->graph_steps - 1;
+            continue;
+        }
         if (h->cfg.interleave) {
             // U^(1/(4 ndim)) before every kinetic block, blocks I'_2 I'_2 I'_1 I'_1 per axis:
             // one fused pass per axis
@@ -1114,6 +1183,15 @@ qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count) {
     return QLGA_OK;
 }
 
+qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    if (steps < 0 || steps % 2 != 0 || steps > 4096) return fail(QLGA_ERR_INVALID_ARG, "graph steps must be even, in 0..4096%s");
+    cudaStreamSynchronize(h->stream);
+    graphs_release(h);
+    h->graph_steps = steps;
+    return QLGA_OK;
+}
+
 qlga_status qlga_synchronize(qlga_handle* h) {
     if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
     QLGA_CUDA(cudaStreamSynchronize(h->stream), "qlga_synchronize");
@@ -1123,6 +1201,7 @@ qlga_status qlga_synchronize(qlga_handle* h) {
 qlga_status qlga_destroy(qlga_handle* h) {
     if (!h) return QLGA_OK;
     cudaStreamSynchronize(h->stream);
+    graphs_release(h);
     if (h->owns) {
         cudaFree(h->X[0]);
         cudaFree(h->X[1]);

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "qlga_observables": [_H, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_synchronize": [_H],
     "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
+    "qlga_set_graph_steps": [_H, ctypes.c_int32],
     "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_fields": [_H, _VP, ctypes.c_int],
     "qlga_batch_state_bytes": [ctypes.POINTER(QlgaBatchConfig), ctypes.POINTER(ctypes.c_size_t)],
@@ -225,6 +226,10 @@ def qlga_launch_count(h: int) -> int:
     out = ctypes.c_int64()
     _check(load_library().qlga_launch_count(_H(h), ctypes.byref(out)), "qlga_launch_count")
     return out.value
+
+
+def qlga_set_graph_steps(h: int, steps: int):
+    _check(load_library().qlga_set_graph_steps(_H(h), ctypes.c_int32(int(steps))), "qlga_set_graph_steps")
 
 
 def qlga_synchronize(h: int):
@@ -421,6 +426,10 @@ class Lattice:
         ws = self.adjoint_workspace(nsteps, checkpoint_every)
         self.adjoint_forward(x0, nsteps, checkpoint_every, ws)
         return self.adjoint_backward(cot, nsteps, checkpoint_every, ws)
+
+    def set_graph_steps(self, steps):
+        """Steps per CUDA graph replay (even; 0 turns graphs off)."""
+        qlga_set_graph_steps(self.handle, steps)
 
     def synchronize(self):
         qlga_synchronize(self.handle)

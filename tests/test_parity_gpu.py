@@ -362,3 +362,30 @@ def test_fields(precision, ndim):
                                atol=(1e-12 if precision == 64 else 1e-4))
     # vorticity: phases in FP64 on both sides from the same amplitudes
     np.testing.assert_allclose(got[6:], ref[6:], rtol=0, atol=1e-9 if precision == 64 else 1e-6)
+
+
+@pytest.mark.parametrize("ndim,nx,ny,precision", [(1, 1024, 1, 64), (1, 16384, 1, 32), (2, 128, 64, 32),
+                                                  (2, 40, 24, 64)])
+def test_step_graphs_give_identical_results(ndim, nx, ny, precision):
+    """Small lattices replay runs of fused steps from a captured CUDA graph; the result must be
+    bit-identical to stepping launch by launch, across reads and representation changes."""
+    rng = np.random.default_rng(57 + nx)
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    g = G_SETS[1]
+    outs = []
+    for graph_steps in (32, 0):
+        lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=g)
+        lat.set_graph_steps(graph_steps)
+        lat.load_state(st)
+        lat.step(70)
+        mid = lat.get_state()
+        lat.apply_kinetic()          # flips the buffer parity: the other graph is captured
+        lat.step(65)
+        outs.append((mid, lat.get_state(), lat.observables()["energy"]))
+        lat.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+    with pytest.raises(qlga.QlgaError):
+        with qlga.Lattice(ndim, nx, ny, precision=precision, g=g) as lat:
+            lat.set_graph_steps(3)

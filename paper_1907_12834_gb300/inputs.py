@@ -318,17 +318,19 @@ def dipole_cores(nx: int, ny: int, separation: float, variant: str = "a"):
     return out
 
 
-def kicked_state(psi, eps, cores, velocity, phase_levels=(), phases=None, sigma=16.0):
+def kicked_state(psi, eps, cores, velocity, phase_levels=(), phases=None, sigma=16.0, core_phases=None):
     """Differentiable initial state (torch): the boson field psi (complex numpy [5, ny, nx])
-    with a windowed local kick at each vortex core and a relative phase on some levels.
+    with a windowed local kick and phase at each vortex core and a phase on some levels.
 
-    Core j at (level l_j, x_j, y_j) gets psi_l <- psi_l exp(i v_j . d w_j), d the nearest-image
-    displacement from the core and w_j = exp(-|d|^2 / (2 sigma^2)): a local phase gradient v_j
-    (rad / site) that moves the core with a continuous velocity, unlike the quantised global
-    kicks 2 pi n / L.  Level phase_levels[k] is multiplied by exp(i phases[k]).
-    velocity: torch tensor [ncores, 2]; phases: torch tensor [len(phase_levels)].  Returns the
-    QLGA state a = b = eps psi / 2 as a torch tensor (5, ny, nx, 2, 2) of velocity's dtype and
-    device."""
+    Core j at (level l_j, x_j, y_j) gets psi_l <- psi_l exp(i (v_j . d + phi_j) w_j), d the
+    nearest-image displacement from the core and w_j = exp(-|d|^2 / (2 sigma^2)): a local phase
+    gradient v_j (rad / site) that moves the core with a continuous velocity, unlike the quantised
+    global kicks 2 pi n / L, and a local phase phi_j (the relative phase of the cores).  Level
+    phase_levels[k] is multiplied by exp(i phases[k]) (a level's global phase: for losses that are
+    invariant under the global phase and under rotations about z these are symmetry directions).
+    velocity: torch tensor [ncores, 2]; core_phases: torch tensor [ncores] or None; phases: torch
+    tensor [len(phase_levels)].  Returns the QLGA state a = b = eps psi / 2 as a torch tensor
+    (5, ny, nx, 2, 2) of velocity's dtype and device."""
     import torch
     dev, dt = velocity.device, velocity.dtype
     ny, nx = psi.shape[1], psi.shape[2]
@@ -342,6 +344,8 @@ def kicked_state(psi, eps, cores, velocity, phase_levels=(), phases=None, sigma=
         dy = torch.remainder(y - yc + ny / 2.0, ny) - ny / 2.0
         w = torch.exp(-(dx * dx + dy * dy) / (2.0 * sigma * sigma))
         th = (velocity[j, 0] * dx + velocity[j, 1] * dy) * w
+        if core_phases is not None:
+            th = th + core_phases[j] * w
         theta = theta + torch.nn.functional.one_hot(torch.tensor(lev), 5).to(dt).to(dev)[:, None, None] * th[None]
     for k, lev in enumerate(phase_levels):
         theta = theta + torch.nn.functional.one_hot(torch.tensor(lev), 5).to(dt).to(dev)[:, None, None] * phases[k]

@@ -10,6 +10,8 @@ import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
 
 import oracle
 from paper_1907_12834_gb300 import inputs, qlga

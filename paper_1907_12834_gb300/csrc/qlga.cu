@@ -485,20 +485,20 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
 namespace qlga {
 
 inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
-    return nx % kStep2dW == 0 && nx >= kStep2dW && ny >= 1 && nx <= (int64_t(1) << 30) &&
+    return nx % kStep2dWarpCols == 0 && nx >= kStep2dWarpCols && ny >= 1 && nx <= (int64_t(1) << 30) &&
            ny <= (int64_t(1) << 30);
 }
 
-// Chunks per strip so that the grid fills every SM once at the kernel's occupancy.
-inline int step2d_chunks(int64_t nx, int64_t ny, int sms, int per_sm) {
-    const int64_t strips = nx / kStep2dW;
+// Row chunks per strip so that the grid fills every SM once at the kernel's occupancy (per_sm
+// resident warp strips per SM).
+inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm) {
     int64_t chunks = (int64_t(sms) * per_sm) / strips;
     if (chunks < 1) chunks = 1;
     if (chunks > ny) chunks = ny;
     return int(chunks);
 }
 
-// Per-device launch facts (SM count, resident CTAs per SM), set up once per device.  The
+// Per-device launch facts (SM count, resident warp strips per SM), set up once per device.  The
 // shared-memory opt-in is a per-device function attribute, so it is applied on each device.
 struct Step2dDevice {
     int sms = 0, per_sm = 0;
@@ -513,14 +513,16 @@ inline int step2d_device(Step2dDevice* out) {
     std::lock_guard<std::mutex> lock(mu);
     Step2dDevice& d = cache[dev];
     if (d.sms == 0) {
-        int sms = 0, per_sm = 0;
+        int sms = 0, ctas = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStep2dSmemBytes) != cudaSuccess) return 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step2d_f32<0, true>, kStep2dW, kStep2dSmemBytes) != cudaSuccess) return 1;
-        d.per_sm = per_sm > 0 ? per_sm : 1;
+        const int smem = kStep2dWarpSmemBytes;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_step2d_f32<0, true>, kStep2dWarpsPerCta * 32, smem) != cudaSuccess)
+            return 1;
+        d.per_sm = ctas > 0 ? ctas * kStep2dWarpsPerCta : 1;
         d.sms = sms;
     }
     *out = d;
@@ -533,14 +535,17 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
                              PotConst<float> PC, unsigned* status, cudaStream_t stream) {
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
-    const int chunks = step2d_chunks(nx, ny, dv.sms, dv.per_sm);
-    const int grid = int(nx / kStep2dW) * chunks;
+    const int64_t strips = nx / kStep2dWarpCols;
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm);
+    const int grid = int((strips * chunks + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta);
+    const dim3 b(kStep2dWarpsPerCta * 32);
+    const int smem = kStep2dWarpSmemBytes;
     if (variant == 0) {
-        if (pot) k_step2d_f32<0, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-        else k_step2d_f32<0, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        if (pot) k_step2d_f32<0, true><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<0, false><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
     } else {
-        if (pot) k_step2d_f32<1, true><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
-        else k_step2d_f32<1, false><<<grid, kStep2dW, kStep2dSmemBytes, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        if (pot) k_step2d_f32<1, true><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f32<1, false><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
     }
     return cudaPeekAtLastError() != cudaSuccess;
 }

@@ -3,12 +3,14 @@
 // out = U(K X) K X with K = K_y K_x (the kinetic blocks I'_1 I'_1 I'_2 I'_2 along x, then along
 // y; Sec. VII.B) and U the potential unitary, for a state held "pending K" (see qlga.cu).
 //
-// Work decomposition ("y-marching strips").  A CTA of kW threads owns a strip of kW columns and a
-// contiguous range of output rows.  Thread t owns column x0 + t and walks down the rows:
-//   1. input rows (with the 4-column x halo on each side, periodic) are staged into a kStages-deep
-//      shared-memory ring with 16-byte cp.async copies, several rows ahead of use;
+// Work decomposition ("y-marching warp strips").  A warp owns a strip of 32 columns and a
+// contiguous range of output rows; lane l owns column x0 + l and walks down the rows:
+//   1. input rows (the 32 columns plus the 4-column x halo on each side, periodic) are staged
+//      into the warp's own kStages-deep shared-memory ring with 16-byte cp.async copies, several
+//      rows ahead of use; warps synchronise only within themselves (__syncwarp), never with each
+//      other, and the halo columns are read by both neighbouring warps (from L2);
 //   2. x axis: the nine-point stencil of one axis (integer coefficients derived at compile time
-//      from the block definition) reads the thread's column and its 8 neighbours from shared
+//      from the block definition) reads the lane's column and its 8 neighbours from shared
 //      memory;
 //   3. y axis: the four blocks I'_2 I'_2 I'_1 I'_1 run as a streaming pipeline down the column:
 //      each block keeps one row of history (the unshifted qubit after the first collide and the
@@ -29,11 +31,8 @@
 
 namespace qlga {
 
-constexpr int kStep2dW = 128;      // columns per strip = threads per CTA
 constexpr int kStep2dStages = 4;   // shared-memory ring depth (rows in flight)
 constexpr int kStep2dHalo = 4;
-constexpr int kStep2dRowSites = kStep2dW + 2 * kStep2dHalo;
-constexpr int kStep2dSmemBytes = kStep2dStages * 5 * kStep2dRowSites * 16;
 
 __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -135,41 +134,51 @@ __device__ __forceinline__ void stencil_tap(const float4 v, float2& xa, float2& 
     xbt = tap<S.g[1][1][K], STYLE>(bt, xbt);
 }
 
-// POT = false: the kinetic operator alone (out = K X), used to read out a state held pending K.
+// The kernel.  POT = false applies the kinetic operator alone (out = K X), used to read out a
+// state held pending K.
+constexpr int kStep2dWarpCols = 32;
+constexpr int kStep2dWarpRowSites = kStep2dWarpCols + 2 * kStep2dHalo;  // 40
+constexpr int kStep2dWarpsPerCta = 4;
+constexpr int kStep2dWarpSmemBytes =
+    kStep2dWarpsPerCta * kStep2dStages * 5 * kStep2dWarpRowSites * 16;
+
 template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
-__global__ void __launch_bounds__(kStep2dW, 3)
+__global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
     k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
-                 PotConst<float> PC, unsigned* status) {
-    extern __shared__ float4 ring[];  // [kStages][5][kRowSites]
-    const int t = threadIdx.x;
-    const int strips = nx / kStep2dW;
-    const int strip = blockIdx.x % strips;
-    const int chunk = blockIdx.x / strips;
-    const int x0 = strip * kStep2dW;
+                  PotConst<float> PC, unsigned* status) {
+    extern __shared__ float4 wring[];  // [warp][kStages][5][kStep2dWarpRowSites]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int strips = nx / kStep2dWarpCols;
+    const int gw = blockIdx.x * kStep2dWarpsPerCta + w;
+    if (gw >= strips * chunks) return;  // whole warp: no block-wide barrier follows
+    const int strip = gw % strips;
+    const int chunk = gw / strips;
+    const int x0 = strip * kStep2dWarpCols;
     const int y_begin = int((int64_t(chunk) * ny) / chunks);
     const int y_end = int((int64_t(chunk + 1) * ny) / chunks);
     const int64_t nsites = int64_t(nx) * ny;
     const float4* in4 = reinterpret_cast<const float4*>(in);
     float4* out4 = reinterpret_cast<float4*>(out);
+    float4* ring = wring + w * (kStep2dStages * 5 * kStep2dWarpRowSites);
 
-    // input rows y_begin-4 .. y_end+3, output row = input row - 4.  Thread t stages column t of
-    // the row (plus, for t < 8, halo column 128 + t) for all five levels.
     const int nrows = (y_end - y_begin) + 8;
-    int xm = x0 - kStep2dHalo + t;
+    // ring column r holds lattice column x0 - 4 + r (periodic); lane l stages r = l and, for
+    // l < 8, r = 32 + l
+    int xm = x0 - kStep2dHalo + lane;
     xm = xm < 0 ? xm + nx : xm;
-    int xh = x0 + kStep2dW - kStep2dHalo + t;
+    int xh = x0 + kStep2dWarpCols - kStep2dHalo + lane;
     xh = xh >= nx ? xh - nx : xh;
     auto issue_row = [&](int r) {
-        int y = y_begin - kStep2dHalo + r;  // in [-4, ny + 3], ny >= 8
+        int y = y_begin - kStep2dHalo + r;
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-        float4* dst = ring + (r % kStep2dStages) * (5 * kStep2dRowSites);
+        float4* dst = ring + (r % kStep2dStages) * (5 * kStep2dWarpRowSites);
         const float4* src = in4 + int64_t(y) * nx;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) cp_async_16(dst + m * kStep2dRowSites + t, src + m * nsites + xm);
-        if (t < 2 * kStep2dHalo) {
+        for (int m = 0; m < 5; ++m) cp_async_16(dst + m * kStep2dWarpRowSites + lane, src + m * nsites + xm);
+        if (lane < 2 * kStep2dHalo) {
 #pragma unroll
             for (int m = 0; m < 5; ++m)
-                cp_async_16(dst + m * kStep2dRowSites + kStep2dW + t, src + m * nsites + xh);
+                cp_async_16(dst + m * kStep2dWarpRowSites + kStep2dWarpCols + lane, src + m * nsites + xh);
         }
     };
 
@@ -185,23 +194,22 @@ __global__ void __launch_bounds__(kStep2dW, 3)
 #pragma unroll
         for (int k = 0; k < 4; ++k) st[m][k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
-    const float inv_sigma2 = 1.0f / 65536.0f;  // sigma = 256
+    const float inv_sigma2 = 1.0f / 65536.0f;
     const float out_scale = 0.5f / 256.0f;
 
     for (int r = 0; r < nrows; ++r) {
         cp_async_wait<kStep2dStages - 2>();
-        __syncthreads();
+        __syncwarp();
         if (r + kStep2dStages - 1 < nrows) issue_row(r + kStep2dStages - 1);
         cp_async_commit();
 
-        const float4* row = ring + (r % kStep2dStages) * (5 * kStep2dRowSites);
+        const float4* row = ring + (r % kStep2dStages) * (5 * kStep2dWarpRowSites);
         cpx<float> oa[5], ob[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            // x axis: nine-point stencil (x16, unnormalised) in the (a, bt) basis
-            const float4* p = row + m * kStep2dRowSites + t;
+            const float4* p = row + m * kStep2dWarpRowSites + lane;
             float2 xa = make_float2(0.f, 0.f), xbt = make_float2(0.f, 0.f);
-            float2 ya = make_float2(0.f, 0.f), ybt = make_float2(0.f, 0.f);  // second accumulators
+            float2 ya = make_float2(0.f, 0.f), ybt = make_float2(0.f, 0.f);
             stencil_tap<VARIANT, 0, STYLE>(p[0], xa, xbt);
             stencil_tap<VARIANT, 1, STYLE>(p[1], ya, ybt);
             stencil_tap<VARIANT, 2, STYLE>(p[2], xa, xbt);
@@ -213,28 +221,27 @@ __global__ void __launch_bounds__(kStep2dW, 3)
             stencil_tap<VARIANT, 8, STYLE>(p[8], xa, xbt);
             xa = p_add<STYLE>(xa, ya);
             xbt = p_add<STYLE>(xbt, ybt);
-            // y axis: I'_2 I'_2 then I'_1 I'_1 as a streaming pipeline (x16, unnormalised)
             stream_block<1, VARIANT, STYLE>(xa, xbt, st[m][0]);
             stream_block<1, VARIANT, STYLE>(xa, xbt, st[m][1]);
             stream_block<0, VARIANT, STYLE>(xa, xbt, st[m][2]);
             stream_block<0, VARIANT, STYLE>(xa, xbt, st[m][3]);
             oa[m] = {xa.x, xa.y};
-            ob[m] = {xbt.y, -xbt.x};  // b = -i bt
+            ob[m] = {xbt.y, -xbt.x};
         }
-        if (r >= 8) {  // pipeline full: this is output row y_begin + r - 8
+        if (r >= 8) {
             if (POT) {
                 potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
             } else {
-                const float s = 1.0f / 256.0f;  // exact: undo the unnormalised collides
+                const float s = 1.0f / 256.0f;
 #pragma unroll
                 for (int m = 0; m < 5; ++m) {
                     oa[m] = s * oa[m];
                     ob[m] = s * ob[m];
                 }
             }
-            const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + t;
+            const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + lane;
 #pragma unroll
-            for (int m = 0; m < 5; ++m)  // resident layout: (a, bt = i b)
+            for (int m = 0; m < 5; ++m)
                 out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
         }
     }

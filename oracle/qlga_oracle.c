@@ -26,6 +26,11 @@
  *  - S_c moves qubit c one site toward +x: c(j) <- c(j-1); S^T_c the other way;
  *  - one axis of the kinetic operator is I'_1 I'_1 I'_2 I'_2 (Sec. VII.B), so the I'_2
  *    blocks act first; in 2D the x axis acts before the y axis.
+ *
+ * Besides the forward step, the file holds the reverse-mode adjoint of the plain step (pull-back
+ * of a cotangent through K and through the linearised potential unitary, with the Frechet
+ * derivative of the matrix exponential taken in the eigenbasis of V), and per-site diagnostic
+ * fields.  Each function states the passage or the derivation it follows.
  */
 #include <complex.h>
 #include <math.h>

@@ -182,9 +182,21 @@ def cpu_baseline(state_f64, g, budget_s, n_sub=256):
     t0 = time.perf_counter()
     oracle.step(win, cfg, steps, nthreads=cores)
     dt = time.perf_counter() - t0
+    # the same oracle on one core, a 64 x 64 window of the same state, about 3 s
+    n1 = 64
+    win1 = np.ascontiguousarray(win[:, :n1, :n1])
+    cfg1 = oracle.make_cfg(2, n1, n1, *g)
+    t0 = time.perf_counter()
+    oracle.step(win1, cfg1, 1, nthreads=1)
+    s1 = max(1, min(100, int(3.0 / max(time.perf_counter() - t0, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step(win1, cfg1, s1, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n_sub * n_sub * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d x %d window at the lattice centre of the same workload, %d FP64 steps, "
-                      "%.1f s" % (n_sub, n_sub, steps, dt)}
+                      "%.1f s" % (n_sub, n_sub, steps, dt),
+            "single_core": {"value": n1 * n1 * s1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": "%d x %d window of the same state, %d FP64 steps, %.1f s" % (n1, n1, s1, dt1)}}
 
 
 # ----------------------------------------------------------------------------- library arm

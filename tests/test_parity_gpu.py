@@ -108,9 +108,10 @@ def test_steps_fp32(ndim, nx, ny, g):
     assert rel_l2(got, ref) <= 1e-5                      # what the arithmetic gives here
 
 
-# nx a multiple of 128: these run the fused single-pass 2D kernel (strips of 128 columns,
-# row chunks with a ragged last chunk, periodic x halo across the strip edges)
-@pytest.mark.parametrize("nx,ny", [(128, 8), (256, 67), (384, 41), (512, 300)])
+# nx a multiple of 32: these run the fused single-pass 2D kernel (warp strips of 32 columns,
+# row chunks with a ragged last chunk, periodic x halo across the strip edges; nx = 32 is one
+# strip whose halo wraps onto itself)
+@pytest.mark.parametrize("nx,ny", [(32, 8), (96, 13), (128, 8), (256, 67), (384, 41), (512, 300)])
 @pytest.mark.parametrize("variant", [0, 1])
 def test_steps_fp32_fused_2d(nx, ny, variant):
     rng = np.random.default_rng(43 + nx + ny)

@@ -285,7 +285,10 @@ def run_gb300(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32},
+                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
+                     "note": "the fused step is limited by FP32 FMA-pipe cycles of the potential "
+                             "(ncu on the settled state: FMA pipe 61% busy, DRAM 36%; "
+                             "profiles/step2d_f32_2048_full.md), not by HBM traffic"},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,

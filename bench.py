@@ -358,7 +358,8 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     sec1 = _timed_steps(torch, lat, 200)
     lat.close()
     out["batched_fp32_1d"] = {"runs": int(len(bw.lengths)), "sites": total, "site_updates_per_s": total / sec,
-                              "ms_per_step": sec * 1e3, "tile_width": info["tile_width"]}
+                              "ms_per_step": sec * 1e3, "tile_width": info["tile_width"],
+                              "sites_per_thread": info["sites_per_thread"]}
     out["single_run_fp64_1d"] = {"lattice": L, "site_updates_per_s": L / sec1, "ms_per_step": sec1 * 1e3}
     out["batched_fp32_over_single_run_fp64"] = (total / sec) / (L / sec1)
     # adjoint on the 512^2 lattice: 200 steps forward with checkpoints every 100, then the pull-back

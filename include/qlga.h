@@ -254,8 +254,8 @@ qlga_status qlga_adjoint_step(qlga_handle* h, const void* x_device, void* cot_de
  * couplings, advanced together (one fused pass over all of them per step).  The state buffer of
  * a batch is the concatenation of the runs' 1D states, each in the layout above with ny = 1
  * (run r starts at element 20 * sum_{s<r} L_s).  Steps are the plain step; the first
- * qlga_batch_step() times the candidate tile widths on the live state (writing only work space)
- * and keeps the fastest; on a non-default stream, pairs of steps are then replayed from a
+ * qlga_batch_step() times the candidate launch shapes (tile widths 64 / 128 / 256 sites, 1 / 2 / 4
+ * sites per thread) on the live state (writing only work space) and keeps the fastest; on a non-default stream, pairs of steps are then replayed from a
  * CUDA graph captured once.
  * --------------------------------------------------------------------------------------- */
 typedef struct qlga_batch_config {
@@ -286,10 +286,11 @@ qlga_status qlga_batch_step(qlga_batch* b, int64_t n);
 /* Observables of every run: out is a host array of nruns qlga_obs (FP64 sums); waits. */
 qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out);
 
-/* Tile width chosen by the tuner (0 before the first step), kernels launched, and the number of
- * steps taken through graph replays. */
-qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int64_t* launches,
-                            int64_t* graph_steps);
+/* Launch shape chosen by the tuner (0 before the first step): tile width in sites and sites per
+ * thread (the CTA has tile_width / sites_per_thread threads); kernels launched, and the number of
+ * steps taken through graph replays.  Any pointer may be NULL. */
+qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int32_t* sites_per_thread,
+                            int64_t* launches, int64_t* graph_steps);
 
 qlga_status qlga_batch_destroy(qlga_batch* b);
 

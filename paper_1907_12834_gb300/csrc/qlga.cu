@@ -1457,7 +1457,14 @@ qlga_status qlga_adjoint_run(qlga_handle* h, const void* x0_device, int64_t nste
 
 namespace {
 
-constexpr int kBatchWidths[3] = {64, 128, 256};
+constexpr int kBatchWidths[3] = {64, 128, 256};  // tile widths (sites), one tile table each
+
+// Launch shapes the tuner times: tile table, threads per CTA, sites per thread.
+struct BatchCand {
+    int tile, threads, spt;
+};
+constexpr BatchCand kBatchCands[6] = {{0, 64, 1}, {1, 128, 1}, {2, 256, 1}, {1, 64, 2}, {2, 128, 2}, {2, 64, 4}};
+constexpr int kBatchNumCands = 6;
 
 }  // namespace
 
@@ -1475,7 +1482,7 @@ struct qlga_batch {
     unsigned* status;
     BatchTile* tiles[3];
     int ntiles[3];
-    int wsel;                 // index into kBatchWidths, -1 before tuning
+    int wsel;                 // index into kBatchCands, -1 before tuning
     int cur;
     bool pending_k;
     int64_t step, launches, graph_steps;
@@ -1507,18 +1514,22 @@ qlga_status check_batch_cfg(const qlga_batch_config* c, int64_t* total) {
     return QLGA_OK;
 }
 
-template <class T, int V, bool POT, int W>
-void batch_launch_t(qlga_batch* b, const void* in, void* out, int wi) {
-    k_batch_step<T, V, POT, W><<<b->ntiles[wi], W, 0, b->stream>>>(
-        static_cast<const T*>(in), static_cast<T*>(out), b->tiles[wi], b->runs,
+template <class T, int V, bool POT, int W, int SPT>
+void batch_launch_t(qlga_batch* b, const void* in, void* out, int tile) {
+    k_batch_step<T, V, POT, W, SPT><<<b->ntiles[tile], W, 0, b->stream>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), b->tiles[tile], b->runs,
         static_cast<const PotConst<T>*>(b->consts), b->status);
 }
 
 template <class T, int V, bool POT>
-void batch_launch_w(qlga_batch* b, const void* in, void* out, int wi) {
-    if (wi == 0) batch_launch_t<T, V, POT, 64>(b, in, out, wi);
-    else if (wi == 1) batch_launch_t<T, V, POT, 128>(b, in, out, wi);
-    else batch_launch_t<T, V, POT, 256>(b, in, out, wi);
+void batch_launch_w(qlga_batch* b, const void* in, void* out, int ci) {
+    const BatchCand c = kBatchCands[ci];
+    if (c.threads == 64 && c.spt == 1) batch_launch_t<T, V, POT, 64, 1>(b, in, out, c.tile);
+    else if (c.threads == 128 && c.spt == 1) batch_launch_t<T, V, POT, 128, 1>(b, in, out, c.tile);
+    else if (c.threads == 256 && c.spt == 1) batch_launch_t<T, V, POT, 256, 1>(b, in, out, c.tile);
+    else if (c.threads == 64 && c.spt == 2) batch_launch_t<T, V, POT, 64, 2>(b, in, out, c.tile);
+    else if (c.threads == 128 && c.spt == 2) batch_launch_t<T, V, POT, 128, 2>(b, in, out, c.tile);
+    else batch_launch_t<T, V, POT, 64, 4>(b, in, out, c.tile);
 }
 
 // One fused step (pot) or the kinetic operator alone: in -> out, tile width index wi.
@@ -1588,7 +1599,7 @@ qlga_status batch_tune(qlga_batch* b) {
     QLGA_CUDA(cudaEventCreate(&e1), "tune event");
     float best = 1e30f;
     int besti = 1;
-    for (int wi = 0; wi < 3; ++wi) {
+    for (int wi = 0; wi < kBatchNumCands; ++wi) {
         qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);  // warm
         if (s != QLGA_OK) return s;
         QLGA_CUDA(cudaEventRecord(e0, b->stream), "tune record");
@@ -1843,9 +1854,11 @@ qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out) {
     return QLGA_OK;
 }
 
-qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int64_t* launches, int64_t* graph_steps) {
+qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int32_t* sites_per_thread, int64_t* launches,
+                            int64_t* graph_steps) {
     if (!b) return fail(QLGA_ERR_INVALID_ARG, "batch is NULL%s");
-    if (tile_width) *tile_width = b->wsel >= 0 ? kBatchWidths[b->wsel] : 0;
+    if (tile_width) *tile_width = b->wsel >= 0 ? kBatchWidths[kBatchCands[b->wsel].tile] : 0;
+    if (sites_per_thread) *sites_per_thread = b->wsel >= 0 ? kBatchCands[b->wsel].spt : 0;
     if (launches) *launches = b->launches;
     if (graph_steps) *graph_steps = b->graph_steps;
     return QLGA_OK;

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "qlga_device.cuh"
+#include "qlga_step2d.cuh"  // cp.async helpers
 
 namespace qlga {
 
@@ -60,75 +61,83 @@ __device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T
     }
 }
 
-// One fused step (POT) or the kinetic operator alone, for the tiles of a batch.
-template <class T, int VARIANT, bool POT, int W>
+// One fused step (POT) or the kinetic operator alone, for the tiles of a batch.  A CTA of W
+// threads takes a tile of W * SPT consecutive sites of one run (thread t owns sites t, t + W, ...):
+// the tile and its 4-site periodic halo on each side are staged in shared memory with 16-byte
+// cp.async copies, all in flight at once, then each thread computes its SPT sites.
+template <class T, int VARIANT, bool POT, int W, int SPT>
 __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* __restrict__ out,
                                                    const BatchTile* __restrict__ tiles,
                                                    const BatchRun* __restrict__ runs,
                                                    const PotConst<T>* __restrict__ consts,
                                                    unsigned* status) {
-    __shared__ Pair4<T> sm[5][W + 8];
+    constexpr int TW = W * SPT;
+    __shared__ __align__(16) Pair4<T> sm[5][TW + 8];  // 16-byte aligned for cp.async
     constexpr KinStencil S = kStencil[VARIANT];
     const BatchTile tile = tiles[blockIdx.x];
     const BatchRun run = runs[tile.run];
     const int L = run.L;
     const int t = threadIdx.x;
-    // staged column c holds site start - 4 + c of the run (periodic); thread t loads column 4 + t
-    // and threads 0..7 also one halo column (0..3, W+4..W+7).  All loads are issued before use.
+    // staged column c holds site start - 4 + c of the run (periodic)
     auto wrap = [&](int j) {
-        if (L >= W + 8) return j < 0 ? j + L : (j >= L ? j - L : j);  // at most one wrap
+        if (L >= TW + 8) return j < 0 ? j + L : (j >= L ? j - L : j);  // at most one wrap
         j %= L;
         return j < 0 ? j + L : j;
     };
-    const int jm = wrap(tile.start + t);
-    const int ch = t < 4 ? t : W + t;
-    const int jh = wrap(tile.start - 4 + ch);
-    Pair4<T> vm[5], vh[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        vm[m] = load_raw_pair(in, run.base + int64_t(m) * L + jm);
-        if (t < 8) vh[m] = load_raw_pair(in, run.base + int64_t(m) * L + jh);
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        sm[m][4 + t] = vm[m];
-        if (t < 8) sm[m][ch] = vh[m];
-    }
-    __syncthreads();
-    const int j = tile.start + t;
-    cpx<T> oa[5], ob[5];
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const Pair4<T> p = sm[m][t + k];
-            const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
-            const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
-            xa.re = fma(caa, p.v[0], fma(cab, p.v[2], xa.re));
-            xa.im = fma(caa, p.v[1], fma(cab, p.v[3], xa.im));
-            xbt.re = fma(cba, p.v[0], fma(cbb, p.v[2], xbt.re));
-            xbt.im = fma(cba, p.v[1], fma(cbb, p.v[3], xbt.im));
-        }
-        oa[m] = xa;                  // x16, unnormalised
-        ob[m] = {xbt.im, -xbt.re};   // b = -i bt
-    }
-    if (POT) {
-        // all lanes take part (the Taylor degree is a warp maximum); lanes past the run's end
-        // work on a copy of a valid site and store nothing
-        const PotConst<T> C = consts[tile.run];
-        potential_site<T, sizeof(T) == 4>(oa, ob, C, T(1.0 / 256.0), T(0.5 / 16.0), status);
-    } else {
+    auto stage = [&](int c) {
+        const int j = wrap(tile.start - 4 + c);
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            oa[m] = T(1.0 / 16.0) * oa[m];
-            ob[m] = T(1.0 / 16.0) * ob[m];
-        }
-    }
-    if (j < L) {
+            const T* src = in + 4 * (run.base + int64_t(m) * L + j);
+            T* dst = reinterpret_cast<T*>(&sm[m][c]);
 #pragma unroll
-        for (int m = 0; m < 5; ++m)
-            store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+            for (int q = 0; q < int(sizeof(Pair4<T>)) / 16; ++q) cp_async_16(dst + q * (16 / sizeof(T)), src + q * (16 / sizeof(T)));
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) stage(4 + t + k * W);
+    if (t < 8) stage(t < 4 ? t : TW + t);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    const PotConst<T> C = consts[tile.run];
+#pragma unroll 1
+    for (int k = 0; k < SPT; ++k) {
+        const int tt = t + k * W;
+        const int j = tile.start + tt;
+        cpx<T> oa[5], ob[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
+#pragma unroll
+            for (int kk = 0; kk < 9; ++kk) {
+                const Pair4<T> p = sm[m][tt + kk];
+                const T caa = T(S.g[0][0][kk]), cab = T(S.g[0][1][kk]);
+                const T cba = T(S.g[1][0][kk]), cbb = T(S.g[1][1][kk]);
+                xa.re = fma(caa, p.v[0], fma(cab, p.v[2], xa.re));
+                xa.im = fma(caa, p.v[1], fma(cab, p.v[3], xa.im));
+                xbt.re = fma(cba, p.v[0], fma(cbb, p.v[2], xbt.re));
+                xbt.im = fma(cba, p.v[1], fma(cbb, p.v[3], xbt.im));
+            }
+            oa[m] = xa;                  // x16, unnormalised
+            ob[m] = {xbt.im, -xbt.re};   // b = -i bt
+        }
+        if (POT) {
+            // all lanes take part (the Taylor degree is a warp maximum); lanes past the run's end
+            // work on a copy of a valid site and store nothing
+            potential_site<T, sizeof(T) == 4>(oa, ob, C, T(1.0 / 256.0), T(0.5 / 16.0), status);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                oa[m] = T(1.0 / 16.0) * oa[m];
+                ob[m] = T(1.0 / 16.0) * ob[m];
+            }
+        }
+        if (j < L) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m)
+                store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+        }
     }
 }
 

@@ -85,8 +85,8 @@ _SIGNATURES = {
     "qlga_batch_get_state": [_H, _VP, ctypes.c_int],
     "qlga_batch_step": [_H, ctypes.c_int64],
     "qlga_batch_observables": [_H, ctypes.POINTER(QlgaObs)],
-    "qlga_batch_info": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
-                        ctypes.POINTER(ctypes.c_int64)],
+    "qlga_batch_info": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     "qlga_batch_destroy": [_H],
     "qlga_destroy": [_H],
     "qlga_adjoint_workspace_bytes": [_CFG, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
@@ -607,10 +607,11 @@ class Batch1D:
         return [obs_to_dict(o) for o in arr]
 
     def info(self):
-        w, l, g = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
-        _check(load_library().qlga_batch_info(_H(self.handle), ctypes.byref(w), ctypes.byref(l),
-                                              ctypes.byref(g)), "qlga_batch_info")
-        return {"tile_width": w.value, "launches": l.value, "graph_steps": g.value}
+        w, spt, l, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().qlga_batch_info(_H(self.handle), ctypes.byref(w), ctypes.byref(spt),
+                                              ctypes.byref(l), ctypes.byref(g)), "qlga_batch_info")
+        return {"tile_width": w.value, "sites_per_thread": spt.value, "launches": l.value,
+                "graph_steps": g.value}
 
     def close(self):
         if getattr(self, "handle", None):

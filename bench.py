@@ -225,7 +225,7 @@ def run_gb300(args):
     settled = w.state if not args.settle else lat.get_state()
     lat.load_state(settled)
     lat.step(args.warmup)
-    lat.observables()
+    obs0 = lat.observables()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -247,6 +247,13 @@ def run_gb300(args):
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     launches = lat.launch_count() - launches0
+    obs1 = lat.observables()
+    drift = {"norm_qubit_rel": abs(obs1["norm_qubit"] - obs0["norm_qubit"]) / obs0["norm_qubit"],
+             "energy_rel": abs(obs1["energy"] - obs0["energy"]) / abs(obs0["energy"]),
+             "steps": args.steps,
+             "note": "FP32 state, FP64 sums, over the timed steps; the qubit norm is conserved exactly by "
+                     "every step, so its drift is FP32 rounding; the energy of the discretised field is "
+                     "not an exact invariant of the QLGA step"}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -290,6 +297,7 @@ def run_gb300(args):
                              "(ncu on the settled state: FMA pipe 61% busy, DRAM 36%; "
                              "profiles/step2d_f32_2048_full.md), not by HBM traffic"},
         "e2e": e2e,
+        "drift": drift,
         "gpu_launches": launches,
         "clocks": clocks,
     }

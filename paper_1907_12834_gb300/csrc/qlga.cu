@@ -552,6 +552,76 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
 
 }  // namespace qlga
 
+// ===================================================================== tiled 1D step: launch
+//
+// k_batch_step serves the batches and single 1D lattices alike (tile tables or, for a single
+// lattice, tiles computed from the block index).  Its launch shape (threads per CTA, sites per
+// thread, tile width = their product) is picked by timing the candidates on the live state.
+
+namespace qlga {
+
+constexpr int kBatchNumWidths = 4;
+constexpr int kBatchWidths[kBatchNumWidths] = {32, 64, 128, 256};  // tile widths (sites)
+
+struct BatchCand {
+    int tile, threads, spt;  // tile: index into kBatchWidths
+};
+constexpr int kBatchNumCands = 7;
+constexpr BatchCand kBatchCands[kBatchNumCands] = {{0, 32, 1}, {1, 64, 1}, {2, 128, 1}, {3, 256, 1},
+                                                   {2, 64, 2}, {3, 128, 2}, {3, 64, 4}};
+constexpr int kBatchDefaultCand = 1;  // before tuning: 64 threads, one site each
+
+struct TileArgs {
+    cudaStream_t stream;
+    int precision, variant;
+    bool pot;
+    const void* in;
+    void* out;
+    const BatchTile* tiles;  // nullptr: a single lattice of single_L sites
+    int ntiles;
+    const BatchRun* runs;
+    const void* consts;
+    unsigned* status;
+    int64_t single_L;
+    PotParams single_params;
+};
+
+template <class T, int V, bool POT, int W, int SPT>
+void tile_launch_shape(const TileArgs& a) {
+    constexpr int TW = W * SPT;
+    const int nb = a.tiles ? a.ntiles : int((a.single_L + TW - 1) / TW);
+    const PotConst<T> pc = a.tiles ? PotConst<T>() : PotConst<T>(a.single_params);
+    k_batch_step<T, V, POT, W, SPT><<<nb, W, 0, a.stream>>>(
+        static_cast<const T*>(a.in), static_cast<T*>(a.out), a.tiles, a.runs,
+        static_cast<const PotConst<T>*>(a.consts), a.status, int(a.single_L), pc);
+}
+
+template <class T, int V, bool POT>
+void tile_launch_cand(const TileArgs& a, int ci) {
+    switch (ci) {
+        case 0: tile_launch_shape<T, V, POT, 32, 1>(a); break;
+        case 1: tile_launch_shape<T, V, POT, 64, 1>(a); break;
+        case 2: tile_launch_shape<T, V, POT, 128, 1>(a); break;
+        case 3: tile_launch_shape<T, V, POT, 256, 1>(a); break;
+        case 4: tile_launch_shape<T, V, POT, 64, 2>(a); break;
+        case 5: tile_launch_shape<T, V, POT, 128, 2>(a); break;
+        default: tile_launch_shape<T, V, POT, 64, 4>(a); break;
+    }
+}
+
+// Launch k_batch_step with shape ci (errors left in cudaGetLastError()).
+inline void tile_step_launch(const TileArgs& a, int ci) {
+    if (a.precision == 32) {
+        if (a.variant == 0) { if (a.pot) tile_launch_cand<float, 0, true>(a, ci); else tile_launch_cand<float, 0, false>(a, ci); }
+        else { if (a.pot) tile_launch_cand<float, 1, true>(a, ci); else tile_launch_cand<float, 1, false>(a, ci); }
+    } else {
+        if (a.variant == 0) { if (a.pot) tile_launch_cand<double, 0, true>(a, ci); else tile_launch_cand<double, 0, false>(a, ci); }
+        else { if (a.pot) tile_launch_cand<double, 1, true>(a, ci); else tile_launch_cand<double, 1, false>(a, ci); }
+    }
+}
+
+}  // namespace qlga
+
 // ===================================================================== handle
 
 struct qlga_handle {
@@ -567,6 +637,7 @@ struct qlga_handle {
     bool pending_k;  // buffer holds X with true state K X
     int64_t step;
     int64_t launches;  // kernels launched by this handle
+    int tile_cand;  // 1D: launch shape of the tiled step (index into kBatchCands), -1 untuned
     // CUDA graphs of graph_steps fused steps starting (and ending) on buffer 0 or 1
     int graph_steps;
     int64_t graph_launches;  // kernels in one graph
@@ -695,10 +766,48 @@ qlga_status launch_interleave(qlga_handle* h, const void* in, void* out, int axi
     return QLGA_OK;
 }
 
+// 1D: the tiled step kernel (shared with the batches) on the whole lattice, in -> out.  The first
+// fused step times the launch shapes on the live state, writing only `out`, and keeps the
+// fastest.
+qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot) {
+    TileArgs a{h->stream, h->cfg.precision, h->cfg.kinetic_variant, pot, in, out, nullptr, 0, nullptr,
+               nullptr, h->status, h->cfg.nx, pot_params(h->cfg, 1.0)};
+    if (pot && h->tile_cand < 0) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        QLGA_CUDA(cudaEventCreate(&e0), "tune event");
+        cudaError_t e = cudaEventCreate(&e1);
+        float best = 1e30f;
+        int besti = kBatchDefaultCand;
+        for (int ci = 0; ci < kBatchNumCands && e == cudaSuccess; ++ci) {
+            tile_step_launch(a, ci);  // warm
+            e = cudaEventRecord(e0, h->stream);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) tile_step_launch(a, ci);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                besti = ci;
+            }
+        }
+        cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e != cudaSuccess) return cuda_fail(e, "1D step tuning");
+        h->launches += 3 * kBatchNumCands;
+        h->tile_cand = besti;
+    }
+    tile_step_launch(a, h->tile_cand >= 0 ? h->tile_cand : kBatchDefaultCand);
+    QLGA_CUDA(cudaGetLastError(), "k_batch_step launch (1D)");
+    h->launches += 1;
+    return QLGA_OK;
+}
+
 // Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
 // x pass.  With pot, U follows the last axis (the fused step).
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
-    if (h->cfg.ndim == 1) return launch_axis(h, in, out, 0, pot);
+    if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
     if (h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
         if (step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx,
                               h->cfg.ny, h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)),
@@ -949,6 +1058,7 @@ static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* str
     h->graph_steps = nsites_of(*cfg) <= kGraphMaxSites ? kGraphDefaultSteps : 0;
     h->graph_launches = 0;
     h->graph[0] = h->graph[1] = nullptr;
+    h->tile_cand = -1;
     QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
     QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
     return QLGA_OK;
@@ -1455,19 +1565,6 @@ qlga_status qlga_adjoint_run(qlga_handle* h, const void* x0_device, int64_t nste
 
 // ===================================================================== batches of 1D lattices
 
-namespace {
-
-constexpr int kBatchWidths[3] = {64, 128, 256};  // tile widths (sites), one tile table each
-
-// Launch shapes the tuner times: tile table, threads per CTA, sites per thread.
-struct BatchCand {
-    int tile, threads, spt;
-};
-constexpr BatchCand kBatchCands[6] = {{0, 64, 1}, {1, 128, 1}, {2, 256, 1}, {1, 64, 2}, {2, 128, 2}, {2, 64, 4}};
-constexpr int kBatchNumCands = 6;
-
-}  // namespace
-
 struct qlga_batch {
     int precision, variant, nruns;
     bool use_graph;
@@ -1480,8 +1577,8 @@ struct qlga_batch {
     double* g3;               // [nruns][3], device
     double* obs_dev;          // [nruns][OBS_COUNT]
     unsigned* status;
-    BatchTile* tiles[3];
-    int ntiles[3];
+    BatchTile* tiles[kBatchNumWidths];
+    int ntiles[kBatchNumWidths];
     int wsel;                 // index into kBatchCands, -1 before tuning
     int cur;
     bool pending_k;
@@ -1514,34 +1611,11 @@ qlga_status check_batch_cfg(const qlga_batch_config* c, int64_t* total) {
     return QLGA_OK;
 }
 
-template <class T, int V, bool POT, int W, int SPT>
-void batch_launch_t(qlga_batch* b, const void* in, void* out, int tile) {
-    k_batch_step<T, V, POT, W, SPT><<<b->ntiles[tile], W, 0, b->stream>>>(
-        static_cast<const T*>(in), static_cast<T*>(out), b->tiles[tile], b->runs,
-        static_cast<const PotConst<T>*>(b->consts), b->status);
-}
-
-template <class T, int V, bool POT>
-void batch_launch_w(qlga_batch* b, const void* in, void* out, int ci) {
-    const BatchCand c = kBatchCands[ci];
-    if (c.threads == 64 && c.spt == 1) batch_launch_t<T, V, POT, 64, 1>(b, in, out, c.tile);
-    else if (c.threads == 128 && c.spt == 1) batch_launch_t<T, V, POT, 128, 1>(b, in, out, c.tile);
-    else if (c.threads == 256 && c.spt == 1) batch_launch_t<T, V, POT, 256, 1>(b, in, out, c.tile);
-    else if (c.threads == 64 && c.spt == 2) batch_launch_t<T, V, POT, 64, 2>(b, in, out, c.tile);
-    else if (c.threads == 128 && c.spt == 2) batch_launch_t<T, V, POT, 128, 2>(b, in, out, c.tile);
-    else batch_launch_t<T, V, POT, 64, 4>(b, in, out, c.tile);
-}
-
-// One fused step (pot) or the kinetic operator alone: in -> out, tile width index wi.
-qlga_status batch_launch(qlga_batch* b, const void* in, void* out, bool pot, int wi) {
-    const bool f = b->precision == 32;
-    if (f) {
-        if (b->variant == 0) { if (pot) batch_launch_w<float, 0, true>(b, in, out, wi); else batch_launch_w<float, 0, false>(b, in, out, wi); }
-        else { if (pot) batch_launch_w<float, 1, true>(b, in, out, wi); else batch_launch_w<float, 1, false>(b, in, out, wi); }
-    } else {
-        if (b->variant == 0) { if (pot) batch_launch_w<double, 0, true>(b, in, out, wi); else batch_launch_w<double, 0, false>(b, in, out, wi); }
-        else { if (pot) batch_launch_w<double, 1, true>(b, in, out, wi); else batch_launch_w<double, 1, false>(b, in, out, wi); }
-    }
+// One fused step (pot) or the kinetic operator alone: in -> out, launch shape ci.
+qlga_status batch_launch(qlga_batch* b, const void* in, void* out, bool pot, int ci) {
+    const TileArgs a{b->stream, b->precision, b->variant, pot, in, out, b->tiles[kBatchCands[ci].tile],
+                     b->ntiles[kBatchCands[ci].tile], b->runs, b->consts, b->status, 0, PotParams{}};
+    tile_step_launch(a, ci);
     QLGA_CUDA(cudaGetLastError(), "k_batch_step launch");
     b->launches += 1;
     return QLGA_OK;
@@ -1581,7 +1655,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchT
 }
 
 qlga_status batch_potential(qlga_batch* b, void* X) {
-    const int wi = 1;  // tiles of 128 sites, 128 threads
+    const int wi = 2;  // tiles of 128 sites, 128 threads
     if (b->precision == 32)
         k_batch_potential<float><<<b->ntiles[wi], 128, 0, b->stream>>>(static_cast<float*>(X), b->tiles[wi], b->runs, static_cast<const PotConst<float>*>(b->consts), kBatchWidths[wi], b->status);
     else
@@ -1598,7 +1672,7 @@ qlga_status batch_tune(qlga_batch* b) {
     QLGA_CUDA(cudaEventCreate(&e0), "tune event");
     QLGA_CUDA(cudaEventCreate(&e1), "tune event");
     float best = 1e30f;
-    int besti = 1;
+    int besti = kBatchDefaultCand;
     for (int wi = 0; wi < kBatchNumCands; ++wi) {
         qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);  // warm
         if (s != QLGA_OK) return s;
@@ -1646,7 +1720,7 @@ qlga_status batch_materialize_view(qlga_batch* b, const void** view) {
         *view = b->X[b->cur];
         return QLGA_OK;
     }
-    qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, false, b->wsel >= 0 ? b->wsel : 1);
+    qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, false, b->wsel >= 0 ? b->wsel : kBatchDefaultCand);
     *view = b->tmp;
     return s;
 }
@@ -1688,8 +1762,8 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
         runs[r].pad = 0;
         base += 5 * cfg->lengths[r];
     }
-    std::vector<BatchTile> tiles[3];
-    for (int wi = 0; wi < 3; ++wi) {
+    std::vector<BatchTile> tiles[kBatchNumWidths];
+    for (int wi = 0; wi < kBatchNumWidths; ++wi) {
         for (int r = 0; r < cfg->nruns; ++r)
             for (int64_t st = 0; st < cfg->lengths[r]; st += kBatchWidths[wi]) tiles[wi].push_back(BatchTile{r, int(st)});
         b->ntiles[wi] = int(tiles[wi].size());
@@ -1703,7 +1777,7 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
     if (e == cudaSuccess) e = cudaMalloc(&b->g3, sizeof(double) * 3 * cfg->nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->obs_dev, sizeof(double) * OBS_COUNT * cfg->nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(unsigned));
-    for (int wi = 0; wi < 3 && e == cudaSuccess; ++wi) e = cudaMalloc(&b->tiles[wi], sizeof(BatchTile) * tiles[wi].size());
+    for (int wi = 0; wi < kBatchNumWidths && e == cudaSuccess; ++wi) e = cudaMalloc(&b->tiles[wi], sizeof(BatchTile) * tiles[wi].size());
     if (e != cudaSuccess) {
         qlga_batch_destroy(b);
         cudaGetLastError();
@@ -1721,7 +1795,7 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
         e = cfg->precision == 32 ? cudaMemcpy(b->consts, cf.data(), cbytes, cudaMemcpyHostToDevice)
                                  : cudaMemcpy(b->consts, cd.data(), cbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->g3, cfg->couplings, sizeof(double) * 3 * cfg->nruns, cudaMemcpyHostToDevice);
-    for (int wi = 0; wi < 3 && e == cudaSuccess; ++wi)
+    for (int wi = 0; wi < kBatchNumWidths && e == cudaSuccess; ++wi)
         e = cudaMemcpy(b->tiles[wi], tiles[wi].data(), sizeof(BatchTile) * tiles[wi].size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->X[0], 0, sb);
     if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(unsigned));
@@ -1876,7 +1950,7 @@ qlga_status qlga_batch_destroy(qlga_batch* b) {
     cudaFree(b->g3);
     cudaFree(b->obs_dev);
     cudaFree(b->status);
-    for (int wi = 0; wi < 3; ++wi) cudaFree(b->tiles[wi]);
+    for (int wi = 0; wi < kBatchNumWidths; ++wi) cudaFree(b->tiles[wi]);
     delete b;
     return QLGA_OK;
 }

@@ -65,17 +65,21 @@ __device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T
 // threads takes a tile of W * SPT consecutive sites of one run (thread t owns sites t, t + W, ...):
 // the tile and its 4-site periodic halo on each side are staged in shared memory with 16-byte
 // cp.async copies, all in flight at once, then each thread computes its SPT sites.
+// tiles == nullptr: one 1D lattice of single_L sites with constants single_pc; tile b starts at
+// site b * W * SPT, and no table is read.
 template <class T, int VARIANT, bool POT, int W, int SPT>
 __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* __restrict__ out,
                                                    const BatchTile* __restrict__ tiles,
                                                    const BatchRun* __restrict__ runs,
                                                    const PotConst<T>* __restrict__ consts,
-                                                   unsigned* status) {
+                                                   unsigned* status, int single_L,
+                                                   PotConst<T> single_pc) {
     constexpr int TW = W * SPT;
     __shared__ __align__(16) Pair4<T> sm[5][TW + 8];  // 16-byte aligned for cp.async
     constexpr KinStencil S = kStencil[VARIANT];
-    const BatchTile tile = tiles[blockIdx.x];
-    const BatchRun run = runs[tile.run];
+    const bool single = tiles == nullptr;
+    const BatchTile tile = single ? BatchTile{0, int(blockIdx.x) * TW} : tiles[blockIdx.x];
+    const BatchRun run = single ? BatchRun{0, single_L, 0} : runs[tile.run];
     const int L = run.L;
     const int t = threadIdx.x;
     // staged column c holds site start - 4 + c of the run (periodic)
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    const PotConst<T> C = consts[tile.run];
+    const PotConst<T> C = single ? single_pc : consts[tile.run];
 #pragma unroll 1
     for (int k = 0; k < SPT; ++k) {
         const int tt = t + k * W;

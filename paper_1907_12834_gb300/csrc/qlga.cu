@@ -766,6 +766,19 @@ qlga_status launch_interleave(qlga_handle* h, const void* in, void* out, int axi
     return QLGA_OK;
 }
 
+// Events that are destroyed when the scope ends, whatever the exit path.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t create() {
+        cudaError_t e = cudaEventCreate(&e0);
+        return e == cudaSuccess ? cudaEventCreate(&e1) : e;
+    }
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // 1D: the tiled step kernel (shared with the batches) on the whole lattice, in -> out.  The first
 // fused step times the launch shapes on the live state, writing only `out`, and keeps the
 // fastest.
@@ -773,27 +786,24 @@ qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot) {
     TileArgs a{h->stream, h->cfg.precision, h->cfg.kinetic_variant, pot, in, out, nullptr, 0, nullptr,
                nullptr, h->status, h->cfg.nx, pot_params(h->cfg, 1.0)};
     if (pot && h->tile_cand < 0) {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        QLGA_CUDA(cudaEventCreate(&e0), "tune event");
-        cudaError_t e = cudaEventCreate(&e1);
+        EventPair ev;
+        cudaError_t e = ev.create();
         float best = 1e30f;
         int besti = kBatchDefaultCand;
         for (int ci = 0; ci < kBatchNumCands && e == cudaSuccess; ++ci) {
             tile_step_launch(a, ci);  // warm
-            e = cudaEventRecord(e0, h->stream);
+            e = cudaEventRecord(ev.e0, h->stream);
             for (int k = 0; k < 2 && e == cudaSuccess; ++k) tile_step_launch(a, ci);
             if (e == cudaSuccess) e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
             float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
             if (e == cudaSuccess && ms < best) {
                 best = ms;
                 besti = ci;
             }
         }
-        cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
         if (e != cudaSuccess) return cuda_fail(e, "1D step tuning");
         h->launches += 3 * kBatchNumCands;
         h->tile_cand = besti;
@@ -1668,30 +1678,27 @@ qlga_status batch_potential(qlga_batch* b, void* X) {
 // Time each tile width on the live state (two fused steps into work space; the state itself is
 // not advanced) and keep the fastest.
 qlga_status batch_tune(qlga_batch* b) {
-    cudaEvent_t e0, e1;
-    QLGA_CUDA(cudaEventCreate(&e0), "tune event");
-    QLGA_CUDA(cudaEventCreate(&e1), "tune event");
+    EventPair ev;
+    QLGA_CUDA(ev.create(), "tune event");
     float best = 1e30f;
     int besti = kBatchDefaultCand;
     for (int wi = 0; wi < kBatchNumCands; ++wi) {
         qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);  // warm
         if (s != QLGA_OK) return s;
-        QLGA_CUDA(cudaEventRecord(e0, b->stream), "tune record");
+        QLGA_CUDA(cudaEventRecord(ev.e0, b->stream), "tune record");
         for (int k = 0; k < 2; ++k) {
             s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);
             if (s != QLGA_OK) return s;
         }
-        QLGA_CUDA(cudaEventRecord(e1, b->stream), "tune record");
-        QLGA_CUDA(cudaEventSynchronize(e1), "tune sync");
+        QLGA_CUDA(cudaEventRecord(ev.e1, b->stream), "tune record");
+        QLGA_CUDA(cudaEventSynchronize(ev.e1), "tune sync");
         float ms = 0.f;
-        QLGA_CUDA(cudaEventElapsedTime(&ms, e0, e1), "tune elapsed");
+        QLGA_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1), "tune elapsed");
         if (ms < best) {
             best = ms;
             besti = wi;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->wsel = besti;
     return QLGA_OK;
 }

@@ -542,6 +542,42 @@ def singlet_fraction(x):
     return (tr * tr + ti * ti).sum() / (rho * rho).sum()
 
 
+def energy(x, g):
+    """Objective: the energy of the boson field psi = a + b of a state tensor (5, ny, nx, 2, 2),
+    as the library's observables define it: sum over sites of sum_axis sum_m |psi_m(j+1) -
+    psi_m(j)|^2 (periodic forward differences) + g0/2 rho^2 + g1/2 |F|^2 + g2/10 |psi^T J psi|^2.
+    g: couplings (g0, g1, g2), floats or a tensor."""
+    import math
+    pr = x[:, :, :, 0, 0] + x[:, :, :, 1, 0]
+    pi = x[:, :, :, 0, 1] + x[:, :, :, 1, 1]
+    grad = 0.0
+    for dim in (2, 1):
+        if x.shape[dim] > 1:
+            grad = grad + ((pr.roll(-1, dims=dim) - pr) ** 2 + (pi.roll(-1, dims=dim) - pi) ** 2).sum()
+    n2 = pr * pr + pi * pi
+    rho = n2.sum(0)
+    Fz = 2 * (n2[0] - n2[4]) + (n2[1] - n2[3])
+    r = math.sqrt(1.5)
+
+    def cc(i, j):  # conj(psi_i) psi_j
+        return pr[i] * pr[j] + pi[i] * pi[j], pr[i] * pi[j] - pi[i] * pr[j]
+    terms = [cc(0, 1), cc(1, 2), cc(2, 3), cc(3, 4)]
+    w = (1.0, r, r, 1.0)
+    Fpr = 2 * sum(wk * t[0] for wk, t in zip(w, terms))
+    Fpi = 2 * sum(wk * t[1] for wk, t in zip(w, terms))
+    F2 = Fz * Fz + Fpr * Fpr + Fpi * Fpi
+
+    def prod(i, j):
+        return pr[i] * pr[j] - pi[i] * pi[j], pr[i] * pi[j] + pi[i] * pr[j]
+    r20, i20 = prod(0, 4)
+    r11, i11 = prod(1, 3)
+    r00, i00 = prod(2, 2)
+    tr = 2 * r20 - 2 * r11 + r00
+    ti = 2 * i20 - 2 * i11 + i00
+    g0, g1, g2 = g[0], g[1], g[2]
+    return grad + (0.5 * g0 * rho * rho + 0.5 * g1 * F2 + 0.1 * g2 * (tr * tr + ti * ti)).sum()
+
+
 # ------------------------------------------------------------------ batches of 1D lattices
 
 def make_batch_config(lengths, couplings, precision=32, epsilon=0.1, kinetic_variant=0,

@@ -370,6 +370,32 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
                               "sites_per_thread": info["sites_per_thread"]}
     out["single_run_fp64_1d"] = {"lattice": L, "site_updates_per_s": L / sec1, "ms_per_step": sec1 * 1e3}
     out["batched_fp32_over_single_run_fp64"] = (total / sec) / (L / sec1)
+    # batched 2D (128 runs of 64..512 x 64..512 sites, FP32) against one FP64 run of the batch
+    b2 = inputs.batch2d()
+    heights = b2.meta["heights"]
+    b = qlga.Batch(b2.lengths, b2.couplings, precision=32, heights=heights)
+    b.load_state(b2.state)
+    b.step(20)
+    torch.cuda.synchronize()
+    e0.record(b.stream)
+    b.step(100)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3 / 100
+    total2 = int((b2.lengths * heights).sum())
+    b.close()
+    r0 = int(np.argsort(b2.lengths * heights)[len(heights) // 2])   # the run of median size
+    o0 = int(20 * (b2.lengths[:r0] * heights[:r0]).sum())
+    nx0, ny0 = int(b2.lengths[r0]), int(heights[r0])
+    lat = qlga.Lattice(2, nx0, ny0, precision=64, g=tuple(b2.couplings[r0]))
+    lat.load_state(b2.state[o0:o0 + 20 * nx0 * ny0].reshape(5, ny0, nx0, 2, 2).astype(np.float64))
+    sec1 = _timed_steps(torch, lat, 20)
+    lat.close()
+    out["batched_fp32_2d"] = {"runs": int(len(heights)), "sites": total2, "site_updates_per_s": total2 / sec,
+                              "ms_per_step": sec * 1e3}
+    out["single_run_fp64_2d"] = {"lattice": [nx0, ny0], "site_updates_per_s": nx0 * ny0 / sec1,
+                                 "ms_per_step": sec1 * 1e3}
+    out["batched_fp32_2d_over_single_run_fp64"] = (total2 / sec) / (nx0 * ny0 / sec1)
     # adjoint on the 512^2 lattice: 200 steps forward with checkpoints every 100, then the pull-back
     for prec in (32, 64):
         w4 = inputs.config4(dtype=np.float32 if prec == 32 else np.float64)

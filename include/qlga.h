@@ -250,22 +250,27 @@ qlga_status qlga_adjoint_step(qlga_handle* h, const void* x_device, void* cot_de
                               size_t workspace_bytes, double* dcoup);
 
 /* ---------------------------------------------------------------------------------------
- * Batches: many independent periodic 1D lattices of uneven length, each with its own
- * couplings, advanced together (one fused pass over all of them per step).  The state buffer of
- * a batch is the concatenation of the runs' 1D states, each in the layout above with ny = 1
- * (run r starts at element 20 * sum_{s<r} L_s).  Steps are the plain step; the first
- * qlga_batch_step() times the candidate launch shapes (tile widths 64 / 128 / 256 sites, 1 / 2 / 4
- * sites per thread) on the live state (writing only work space) and keeps the fastest; on a non-default stream, pairs of steps are then replayed from a
- * CUDA graph captured once.
+ * Batches: many independent periodic lattices of uneven size, 1D and 2D, each with its own
+ * couplings, advanced together.  The state buffer of a batch is the concatenation of the runs'
+ * states, each in the layout above (run r starts at element 20 * sum_{s<r} nx_s ny_s).  Steps are
+ * the plain step.  1D runs go through a tiled kernel in one launch per step; the first
+ * qlga_batch_step() times its candidate launch shapes (tiles of 32 / 64 / 128 / 256 sites,
+ * 1 / 2 / 4 sites per thread) on the live state (writing only work space) and keeps the fastest.
+ * 2D runs (FP32; nx a multiple of 32) go through the fused warp-strip kernel of the single 2D
+ * lattice, its warps reading their run, strip and row range from a task table, in one more
+ * launch per step.  On a non-default stream, pairs of steps are replayed from a CUDA graph
+ * captured once.
  * --------------------------------------------------------------------------------------- */
 typedef struct qlga_batch_config {
-    int32_t precision;       /* 32 or 64 */
+    int32_t precision;       /* 32 or 64 (64: 1D runs only) */
     int32_t nruns;           /* >= 1 */
-    const int64_t* lengths;  /* host array [nruns], each >= 8 and <= 2^30 */
+    const int64_t* lengths;  /* host array [nruns]: nx of each run; a 1D run has 8 <= nx <= 2^30 */
     const double* couplings; /* host array [nruns][3]: g0, g1, g2 of each run */
     double epsilon;          /* lattice scaling (informational for batches) */
     int32_t kinetic_variant; /* QLGA_KINETIC_K1 or QLGA_KINETIC_K2 */
     int32_t use_graph;       /* 1: replay steps from a captured CUDA graph where possible */
+    const int64_t* heights;  /* host array [nruns]: ny of each run (1: a 1D run; a 2D run needs
+                                ny >= 8, nx a multiple of 32, nx * ny <= 2^30), or NULL: all 1D */
 } qlga_batch_config;
 
 typedef struct qlga_batch qlga_batch;

@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_observables(const T* __restr
                                                                 double* __restrict__ out) {
     const BatchRun run = runs[blockIdx.x];
     const int L = run.L;
+    const int ny = run.ny, nx = L / ny;
     const T r32 = T(1.2247448713915890491);
     const T hg0 = T(0.5 * g3[3 * blockIdx.x]), hg1 = T(0.5 * g3[3 * blockIdx.x + 1]);
     const T tg2 = T(0.1 * g3[3 * blockIdx.x + 2]);
@@ -365,10 +366,17 @@ __global__ void __launch_bounds__(kThreads) k_batch_observables(const T* __restr
         const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
         const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
         const T th2 = norm2(th);
-        const int jn = j + 1 == L ? 0 : j + 1;
+        // forward differences along x (and y for a 2D run), periodic within the run
+        const int x = j % nx, y = j / nx;
+        const int jx = y * nx + (x + 1 == nx ? 0 : x + 1);
         T grad = T(0);
 #pragma unroll
-        for (int m = 0; m < 5; ++m) grad += norm2(boson(m, jn) - psi[m]);
+        for (int m = 0; m < 5; ++m) grad += norm2(boson(m, jx) - psi[m]);
+        if (ny > 1) {
+            const int jy = (y + 1 == ny ? 0 : y + 1) * nx + x;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) grad += norm2(boson(m, jy) - psi[m]);
+        }
         acc[OBS_ENERGY].add(grad + hg0 * rho * rho + hg1 * F2 + tg2 * th2);
         acc[OBS_SINGLET_RE].add(th.re * T(0.44721359549995793928));
         acc[OBS_SINGLET_IM].add(th.im * T(0.44721359549995793928));
@@ -520,6 +528,10 @@ inline int step2d_device(Step2dDevice* out) {
         if (cudaFuncSetAttribute(k_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
         if (cudaFuncSetAttribute(k_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
         if (cudaFuncSetAttribute(k_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_batch_step2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_batch_step2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_batch_step2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_batch_step2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_step2d_f32<0, true>, kStep2dWarpsPerCta * 32, smem) != cudaSuccess)
             return 1;
         d.per_sm = ctas > 0 ? ctas * kStep2dWarpsPerCta : 1;
@@ -1587,8 +1599,13 @@ struct qlga_batch {
     double* g3;               // [nruns][3], device
     double* obs_dev;          // [nruns][OBS_COUNT]
     unsigned* status;
-    BatchTile* tiles[kBatchNumWidths];
+    BatchTile* tiles[kBatchNumWidths];  // tiles of the 1D runs, per tile width
     int ntiles[kBatchNumWidths];
+    BatchTile* tiles_pot;     // 128-site tiles over every run (planes of 2D runs flattened)
+    int ntiles_pot;
+    Run2d* runs2d;            // [nruns] (entries of 1D runs unused)
+    WarpTask* tasks;          // warp tasks of the 2D runs
+    int ntasks;
     int wsel;                 // index into kBatchCands, -1 before tuning
     int cur;
     bool pending_k;
@@ -1611,31 +1628,56 @@ qlga_status check_batch_cfg(const qlga_batch_config* c, int64_t* total) {
         return fail(QLGA_ERR_INVALID_ARG, "kinetic_variant must be K1 or K2%s");
     int64_t t = 0;
     for (int r = 0; r < c->nruns; ++r) {
-        if (c->lengths[r] < 8 || c->lengths[r] > (int64_t(1) << 30)) return fail(QLGA_ERR_INVALID_ARG, "run lengths must be in [8, 2^30]%s");
+        const int64_t nx = c->lengths[r], ny = c->heights ? c->heights[r] : 1;
+        if (ny == 1) {
+            if (nx < 8 || nx > (int64_t(1) << 30)) return fail(QLGA_ERR_INVALID_ARG, "1D run lengths must be in [8, 2^30]%s");
+        } else {
+            if (ny < 8 || nx < kStep2dWarpCols || nx % kStep2dWarpCols != 0 || nx * ny > (int64_t(1) << 30))
+                return fail(QLGA_ERR_INVALID_ARG, "2D runs need ny >= 8, nx a multiple of 32 and nx * ny <= 2^30%s");
+            if (c->precision != 32) return fail(QLGA_ERR_UNSUPPORTED, "2D runs in a batch are stepped in FP32 only%s");
+        }
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(c->couplings[3 * r + k])) return fail(QLGA_ERR_INVALID_ARG, "couplings must be finite%s");
-        t += c->lengths[r];
+        t += nx * ny;
     }
     if (t > (int64_t(1) << 34)) return fail(QLGA_ERR_INVALID_ARG, "batch too large%s");
     *total = t;
     return QLGA_OK;
 }
 
-// One fused step (pot) or the kinetic operator alone: in -> out, launch shape ci.
+// One fused step (pot) or the kinetic operator alone: in -> out.  1D runs: the tiled kernel with
+// launch shape ci; 2D runs: the warp-strip kernel over the task table.
 qlga_status batch_launch(qlga_batch* b, const void* in, void* out, bool pot, int ci) {
-    const TileArgs a{b->stream, b->precision, b->variant, pot, in, out, b->tiles[kBatchCands[ci].tile],
-                     b->ntiles[kBatchCands[ci].tile], b->runs, b->consts, b->status, 0, PotParams{}};
-    tile_step_launch(a, ci);
-    QLGA_CUDA(cudaGetLastError(), "k_batch_step launch");
-    b->launches += 1;
+    if (b->ntiles[kBatchCands[ci].tile] > 0) {
+        const TileArgs a{b->stream, b->precision, b->variant, pot, in, out, b->tiles[kBatchCands[ci].tile],
+                         b->ntiles[kBatchCands[ci].tile], b->runs, b->consts, b->status, 0, PotParams{}};
+        tile_step_launch(a, ci);
+        QLGA_CUDA(cudaGetLastError(), "k_batch_step launch");
+        b->launches += 1;
+    }
+    if (b->ntasks > 0) {
+        Step2dDevice dv;
+        if (step2d_device(&dv)) return cuda_fail(cudaGetLastError(), "2D batch set-up");
+        const int grid = (b->ntasks + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta;
+        const dim3 blk(kStep2dWarpsPerCta * 32);
+        const float* fi = static_cast<const float*>(in);
+        float* fo = static_cast<float*>(out);
+        const PotConst<float>* pc = static_cast<const PotConst<float>*>(b->consts);
+        if (b->variant == 0) {
+            if (pot) k_batch_step2d_f32<0, true><<<grid, blk, kStep2dWarpSmemBytes, b->stream>>>(fi, fo, b->tasks, b->ntasks, b->runs2d, pc, b->status);
+            else k_batch_step2d_f32<0, false><<<grid, blk, kStep2dWarpSmemBytes, b->stream>>>(fi, fo, b->tasks, b->ntasks, b->runs2d, pc, b->status);
+        } else {
+            if (pot) k_batch_step2d_f32<1, true><<<grid, blk, kStep2dWarpSmemBytes, b->stream>>>(fi, fo, b->tasks, b->ntasks, b->runs2d, pc, b->status);
+            else k_batch_step2d_f32<1, false><<<grid, blk, kStep2dWarpSmemBytes, b->stream>>>(fi, fo, b->tasks, b->ntasks, b->runs2d, pc, b->status);
+        }
+        QLGA_CUDA(cudaGetLastError(), "k_batch_step2d_f32 launch");
+        b->launches += 1;
+    }
     return QLGA_OK;
 }
 
-// The potential unitary alone from a raw state: a fused step whose kinetic part is skipped is
-// not available, so the first step from a raw state applies U with the generic per-site kernel
-// through a flat view of the batch (U is local, so run boundaries do not matter) -- but each run
-// has its own couplings, so instead the batch keeps raw states raw and applies one fused step
-// of the shifted form: X <- U(X) X is done by the kinetic-free path below.
+// The potential unitary alone, in place (the first step from a raw state): U is local, so it
+// runs over 128-site tiles of every run's flattened planes, with the run's constants.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchTile* __restrict__ tiles,
                                                               const BatchRun* __restrict__ runs,
@@ -1665,11 +1707,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchT
 }
 
 qlga_status batch_potential(qlga_batch* b, void* X) {
-    const int wi = 2;  // tiles of 128 sites, 128 threads
+    // tiles of 128 sites over every run's planes, 128 threads
     if (b->precision == 32)
-        k_batch_potential<float><<<b->ntiles[wi], 128, 0, b->stream>>>(static_cast<float*>(X), b->tiles[wi], b->runs, static_cast<const PotConst<float>*>(b->consts), kBatchWidths[wi], b->status);
+        k_batch_potential<float><<<b->ntiles_pot, 128, 0, b->stream>>>(static_cast<float*>(X), b->tiles_pot, b->runs, static_cast<const PotConst<float>*>(b->consts), 128, b->status);
     else
-        k_batch_potential<double><<<b->ntiles[wi], 128, 0, b->stream>>>(static_cast<double*>(X), b->tiles[wi], b->runs, static_cast<const PotConst<double>*>(b->consts), kBatchWidths[wi], b->status);
+        k_batch_potential<double><<<b->ntiles_pot, 128, 0, b->stream>>>(static_cast<double*>(X), b->tiles_pot, b->runs, static_cast<const PotConst<double>*>(b->consts), 128, b->status);
     QLGA_CUDA(cudaGetLastError(), "k_batch_potential launch");
     b->launches += 1;
     return QLGA_OK;
@@ -1678,6 +1720,10 @@ qlga_status batch_potential(qlga_batch* b, void* X) {
 // Time each tile width on the live state (two fused steps into work space; the state itself is
 // not advanced) and keep the fastest.
 qlga_status batch_tune(qlga_batch* b) {
+    if (b->ntiles[0] == 0) {  // no 1D runs: nothing to tune
+        b->wsel = kBatchDefaultCand;
+        return QLGA_OK;
+    }
     EventPair ev;
     QLGA_CUDA(ev.create(), "tune event");
     float best = 1e30f;
@@ -1762,19 +1808,45 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
     b->graph_cur = -1;
     const size_t sb = batch_state_bytes_of(cfg->precision, total);
     std::vector<BatchRun> runs(cfg->nruns);
+    std::vector<Run2d> runs2d(cfg->nruns);
     int64_t base = 0;
     for (int r = 0; r < cfg->nruns; ++r) {
+        const int64_t nx = cfg->lengths[r], ny = cfg->heights ? cfg->heights[r] : 1;
         runs[r].base = base;
-        runs[r].L = int(cfg->lengths[r]);
-        runs[r].pad = 0;
-        base += 5 * cfg->lengths[r];
+        runs[r].L = int(nx * ny);
+        runs[r].ny = int(ny);
+        runs2d[r] = Run2d{base, int(nx), int(ny)};
+        base += 5 * nx * ny;
     }
-    std::vector<BatchTile> tiles[kBatchNumWidths];
-    for (int wi = 0; wi < kBatchNumWidths; ++wi) {
+    // tile tables of the 1D runs (the tiled kernel), 128-site tiles of every run (the potential)
+    std::vector<BatchTile> tiles[kBatchNumWidths], tiles_pot;
+    for (int r = 0; r < cfg->nruns; ++r) {
+        for (int64_t st = 0; st < runs[r].L; st += 128) tiles_pot.push_back(BatchTile{r, int(st)});
+        if (runs[r].ny != 1) continue;
+        for (int wi = 0; wi < kBatchNumWidths; ++wi)
+            for (int64_t st = 0; st < runs[r].L; st += kBatchWidths[wi]) tiles[wi].push_back(BatchTile{r, int(st)});
+    }
+    for (int wi = 0; wi < kBatchNumWidths; ++wi) b->ntiles[wi] = int(tiles[wi].size());
+    b->ntiles_pot = int(tiles_pot.size());
+    // warp tasks of the 2D runs: 32-column strips x row chunks of about `rows` rows, sized so that
+    // the tasks fill every SM a few times over
+    std::vector<WarpTask> tasks;
+    {
+        int64_t strip_rows = 0;
         for (int r = 0; r < cfg->nruns; ++r)
-            for (int64_t st = 0; st < cfg->lengths[r]; st += kBatchWidths[wi]) tiles[wi].push_back(BatchTile{r, int(st)});
-        b->ntiles[wi] = int(tiles[wi].size());
+            if (runs[r].ny > 1) strip_rows += (runs2d[r].nx / kStep2dWarpCols) * int64_t(runs2d[r].ny);
+        const int64_t target = 152 * 12 * 2;
+        const int64_t rows = std::max<int64_t>(16, (strip_rows + target - 1) / std::max<int64_t>(target, 1));
+        for (int r = 0; r < cfg->nruns; ++r) {
+            if (runs[r].ny == 1) continue;
+            const int ny = runs2d[r].ny;
+            const int chunks = int(std::max<int64_t>(1, (ny + rows / 2) / rows));
+            for (int c = 0; c < chunks; ++c)
+                for (int x0 = 0; x0 < runs2d[r].nx; x0 += kStep2dWarpCols)
+                    tasks.push_back(WarpTask{r, x0, int((int64_t(c) * ny) / chunks), int((int64_t(c + 1) * ny) / chunks)});
+        }
     }
+    b->ntasks = int(tasks.size());
     const size_t cbytes = size_t(cfg->nruns) * (cfg->precision == 32 ? sizeof(PotConst<float>) : sizeof(PotConst<double>));
     cudaError_t e = cudaMalloc(&b->X[0], sb);
     if (e == cudaSuccess) e = cudaMalloc(&b->X[1], sb);
@@ -1784,7 +1856,11 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
     if (e == cudaSuccess) e = cudaMalloc(&b->g3, sizeof(double) * 3 * cfg->nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->obs_dev, sizeof(double) * OBS_COUNT * cfg->nruns);
     if (e == cudaSuccess) e = cudaMalloc(&b->status, sizeof(unsigned));
-    for (int wi = 0; wi < kBatchNumWidths && e == cudaSuccess; ++wi) e = cudaMalloc(&b->tiles[wi], sizeof(BatchTile) * tiles[wi].size());
+    for (int wi = 0; wi < kBatchNumWidths && e == cudaSuccess; ++wi)
+        e = cudaMalloc(&b->tiles[wi], sizeof(BatchTile) * std::max<size_t>(1, tiles[wi].size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->tiles_pot, sizeof(BatchTile) * tiles_pot.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->runs2d, sizeof(Run2d) * runs2d.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->tasks, sizeof(WarpTask) * std::max<size_t>(1, tasks.size()));
     if (e != cudaSuccess) {
         qlga_batch_destroy(b);
         cudaGetLastError();
@@ -1803,7 +1879,13 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
                                  : cudaMemcpy(b->consts, cd.data(), cbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->g3, cfg->couplings, sizeof(double) * 3 * cfg->nruns, cudaMemcpyHostToDevice);
     for (int wi = 0; wi < kBatchNumWidths && e == cudaSuccess; ++wi)
-        e = cudaMemcpy(b->tiles[wi], tiles[wi].data(), sizeof(BatchTile) * tiles[wi].size(), cudaMemcpyHostToDevice);
+        if (!tiles[wi].empty())
+            e = cudaMemcpy(b->tiles[wi], tiles[wi].data(), sizeof(BatchTile) * tiles[wi].size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->tiles_pot, tiles_pot.data(), sizeof(BatchTile) * tiles_pot.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->runs2d, runs2d.data(), sizeof(Run2d) * runs2d.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tasks.empty())
+        e = cudaMemcpy(b->tasks, tasks.data(), sizeof(WarpTask) * tasks.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->X[0], 0, sb);
     if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) {
@@ -1958,6 +2040,9 @@ qlga_status qlga_batch_destroy(qlga_batch* b) {
     cudaFree(b->obs_dev);
     cudaFree(b->status);
     for (int wi = 0; wi < kBatchNumWidths; ++wi) cudaFree(b->tiles[wi]);
+    cudaFree(b->tiles_pot);
+    cudaFree(b->runs2d);
+    cudaFree(b->tasks);
     delete b;
     return QLGA_OK;
 }

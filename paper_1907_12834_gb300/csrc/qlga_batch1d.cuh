@@ -27,8 +27,8 @@ struct BatchTile {
 
 struct BatchRun {
     int64_t base;  // pair index of plane 0, site 0 of the run
-    int L;
-    int pad;
+    int L;         // sites of one plane: nx for a 1D run, nx * ny for a 2D run
+    int ny;        // 1 for a 1D run
 };
 
 template <class T>
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
     constexpr KinStencil S = kStencil[VARIANT];
     const bool single = tiles == nullptr;
     const BatchTile tile = single ? BatchTile{0, int(blockIdx.x) * TW} : tiles[blockIdx.x];
-    const BatchRun run = single ? BatchRun{0, single_L, 0} : runs[tile.run];
+    const BatchRun run = single ? BatchRun{0, single_L, 1} : runs[tile.run];
     const int L = run.L;
     const int t = threadIdx.x;
     // staged column c holds site start - 4 + c of the run (periodic)

@@ -134,32 +134,22 @@ __device__ __forceinline__ void stencil_tap(const float4 v, float2& xa, float2& 
     xbt = tap<S.g[1][1][K], STYLE>(bt, xbt);
 }
 
-// The kernel.  POT = false applies the kinetic operator alone (out = K X), used to read out a
-// state held pending K.
+// Launch geometry: warps of 32 columns, 4 warps per CTA, each warp with its own ring.
 constexpr int kStep2dWarpCols = 32;
 constexpr int kStep2dWarpRowSites = kStep2dWarpCols + 2 * kStep2dHalo;  // 40
 constexpr int kStep2dWarpsPerCta = 4;
 constexpr int kStep2dWarpSmemBytes =
     kStep2dWarpsPerCta * kStep2dStages * 5 * kStep2dWarpRowSites * 16;
 
-template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
-__global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
-    k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
-                  PotConst<float> PC, unsigned* status) {
-    extern __shared__ float4 wring[];  // [warp][kStages][5][kStep2dWarpRowSites]
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int strips = nx / kStep2dWarpCols;
-    const int gw = blockIdx.x * kStep2dWarpsPerCta + w;
-    if (gw >= strips * chunks) return;  // whole warp: no block-wide barrier follows
-    const int strip = gw % strips;
-    const int chunk = gw / strips;
-    const int x0 = strip * kStep2dWarpCols;
-    const int y_begin = int((int64_t(chunk) * ny) / chunks);
-    const int y_end = int((int64_t(chunk + 1) * ny) / chunks);
+// One warp's work: the strip of columns [x0, x0 + 32) of an nx x ny lattice and output rows
+// [y_begin, y_end); `ring` is the warp's shared-memory ring.
+template <int VARIANT, bool POT, int STYLE>
+__device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float* __restrict__ out, int nx,
+                                             int ny, int x0, int y_begin, int y_end, const PotConst<float>& PC,
+                                             unsigned* status, float4* ring, int lane) {
     const int64_t nsites = int64_t(nx) * ny;
     const float4* in4 = reinterpret_cast<const float4*>(in);
     float4* out4 = reinterpret_cast<float4*>(out);
-    float4* ring = wring + w * (kStep2dStages * 5 * kStep2dWarpRowSites);
 
     const int nrows = (y_end - y_begin) + 8;
     // ring column r holds lattice column x0 - 4 + r (periodic); lane l stages r = l and, for
@@ -168,6 +158,7 @@ __global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
     xm = xm < 0 ? xm + nx : xm;
     int xh = x0 + kStep2dWarpCols - kStep2dHalo + lane;
     xh = xh >= nx ? xh - nx : xh;
+    xh = xh >= nx ? xh - nx : xh;  // nx = 32: the right halo wraps onto the strip itself
     auto issue_row = [&](int r) {
         int y = y_begin - kStep2dHalo + r;
         y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
@@ -246,6 +237,54 @@ __global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
         }
     }
     cp_async_wait<0>();
+}
+
+// The kernel.  POT = false applies the kinetic operator alone (out = K X), used to read out a
+// state held pending K.  Warp gw of the grid takes strip gw % strips of row chunk gw / strips.
+template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
+__global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
+    k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,
+                 PotConst<float> PC, unsigned* status) {
+    extern __shared__ float4 wring[];  // [warp][kStages][5][kStep2dWarpRowSites]
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int strips = nx / kStep2dWarpCols;
+    const int gw = blockIdx.x * kStep2dWarpsPerCta + w;
+    if (gw >= strips * chunks) return;  // whole warp: no block-wide barrier follows
+    const int strip = gw % strips;
+    const int chunk = gw / strips;
+    const int y_begin = int((int64_t(chunk) * ny) / chunks);
+    const int y_end = int((int64_t(chunk + 1) * ny) / chunks);
+    step2d_strip<VARIANT, POT, STYLE>(in, out, nx, ny, strip * kStep2dWarpCols, y_begin, y_end, PC, status,
+                                      wring + w * (kStep2dStages * 5 * kStep2dWarpRowSites), lane);
+}
+
+// A batch of 2D lattices: warp gw takes task gw of the table -- a run (its state at pair offset
+// base, nx x ny sites, constants consts[run]), a strip and a row range.
+struct WarpTask {
+    int run;
+    int x0;
+    int y_begin, y_end;
+};
+struct Run2d {
+    int64_t base;  // pair index of plane 0, site 0 of the run
+    int nx, ny;
+};
+
+template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
+__global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
+    k_batch_step2d_f32(const float* __restrict__ in, float* __restrict__ out,
+                       const WarpTask* __restrict__ tasks, int ntasks, const Run2d* __restrict__ runs,
+                       const PotConst<float>* __restrict__ consts, unsigned* status) {
+    extern __shared__ float4 wring[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kStep2dWarpsPerCta + w;
+    if (gw >= ntasks) return;  // whole warp
+    const WarpTask task = tasks[gw];
+    const Run2d run = runs[task.run];
+    const PotConst<float> PC = consts[task.run];
+    step2d_strip<VARIANT, POT, STYLE>(in + 4 * run.base, out + 4 * run.base, run.nx, run.ny, task.x0,
+                                      task.y_begin, task.y_end, PC, status,
+                                      wring + w * (kStep2dStages * 5 * kStep2dWarpRowSites), lane);
 }
 
 }  // namespace qlga

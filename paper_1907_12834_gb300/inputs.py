@@ -400,3 +400,29 @@ def config3(seed: int = 1910, nruns: int = 256, lmin: int = 2048, lmax: int = 65
     parts = [boson_to_state(scattering_run(rng, int(L), eps), eps, dtype=dtype).ravel() for L in lengths]
     return BatchWorkload("1d-batched-scattering-%druns" % nruns, lengths, couplings, eps, steps,
                          32 if dtype == np.float32 else 64, np.concatenate(parts))
+
+
+def batch2d(seed: int = 1912, nruns: int = 128, eps: float = 0.1, steps: int = 2000,
+            dtype=np.float32) -> BatchWorkload:
+    """Batched 2D vortex scattering: nruns independent runs of uneven size, nx = 32 k with k
+    uniform in 2..16 (64 .. 512 columns), ny log-uniform in [64, 512]; each run holds the config 2
+    dipole pair (variant a, cores nx / 4 apart, seeded integer kicks) at couplings g0 = 1 and
+    g1, g2 uniform in [0.05, 0.5] x [0.5, 1.5] (the regime of the paper's 2D runs).  The state is
+    the concatenation of the runs' 2D states; `meta["heights"]` holds each run's ny."""
+    rng = np.random.default_rng(seed)
+    nx = 32 * rng.integers(2, 17, size=nruns)
+    ny = np.exp(rng.uniform(np.log(64), np.log(512), size=nruns)).astype(np.int64)
+    couplings = np.column_stack([np.ones(nruns), rng.uniform(0.05, 0.5, nruns), rng.uniform(0.5, 1.5, nruns)])
+    parts = []
+    for r in range(nruns):
+        g = tuple(couplings[r])
+        psi = np.zeros((5, int(ny[r]), int(nx[r])), dtype=np.complex128)
+        for k, mf in enumerate((2, -2)):
+            kick = tuple(int(v) for v in rng.integers(-2, 3, size=2))
+            psi[2 - mf] = vortex_dipole(int(nx[r]), int(ny[r]), eps, mf, CONFIG2_G, separation=nx[r] / 4.0,
+                                        winding=+1 if k == 0 else -1, kick=kick)
+        parts.append(boson_to_state(psi, eps, dtype=dtype).ravel())
+    w = BatchWorkload("2d-batched-vortex-scattering-%druns" % nruns, nx.astype(np.int64), couplings, eps, steps,
+                      32 if dtype == np.float32 else 64, np.concatenate(parts))
+    w.meta["heights"] = ny.astype(np.int64)
+    return w

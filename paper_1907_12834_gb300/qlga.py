@@ -45,7 +45,8 @@ class QlgaBatchConfig(ctypes.Structure):
                 ("lengths", ctypes.POINTER(ctypes.c_int64)),
                 ("couplings", ctypes.POINTER(ctypes.c_double)),
                 ("epsilon", ctypes.c_double), ("kinetic_variant", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32),
+                ("heights", ctypes.POINTER(ctypes.c_int64))]
 
 
 class QlgaError(RuntimeError):
@@ -448,6 +449,7 @@ class Lattice:
         except Exception:
             pass
 
+
     def __enter__(self):
         return self
 
@@ -581,14 +583,17 @@ def energy(x, g):
 # ------------------------------------------------------------------ batches of 1D lattices
 
 def make_batch_config(lengths, couplings, precision=32, epsilon=0.1, kinetic_variant=0,
-                      use_graph=True):
-    """Returns (config, keepalive arrays) -- the arrays must outlive the create call."""
+                      use_graph=True, heights=None):
+    """Returns (config, keepalive arrays) -- the arrays must outlive the create call.
+    lengths: nx of each run; heights: ny of each run (None: every run is 1D)."""
     L = np.ascontiguousarray(lengths, dtype=np.int64)
     G = np.ascontiguousarray(couplings, dtype=np.float64).reshape(len(L), 3)
+    H = None if heights is None else np.ascontiguousarray(heights, dtype=np.int64)
     cfg = QlgaBatchConfig(int(precision), len(L), L.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                           G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(epsilon),
-                          int(kinetic_variant), int(bool(use_graph)))
-    return cfg, (L, G)
+                          int(kinetic_variant), int(bool(use_graph)),
+                          None if H is None else H.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return cfg, (L, G, H)
 
 
 def qlga_batch_state_bytes(cfg) -> int:
@@ -598,20 +603,21 @@ def qlga_batch_state_bytes(cfg) -> int:
     return out.value
 
 
-class Batch1D:
-    """Many periodic 1D lattices of uneven length, advanced together (one fused pass per step).
+class Batch:
+    """Many periodic lattices of uneven size (1D runs, and 2D runs in FP32), advanced together.
 
-    The state is the concatenation of the runs' 1D states in the library layout, as a flat
-    float32 / float64 array (see inputs.BatchWorkload)."""
+    The state is the concatenation of the runs' states in the library layout, as a flat
+    float32 / float64 array (see inputs.BatchWorkload); run r holds 20 * nx_r * ny_r reals."""
 
     def __init__(self, lengths, couplings, precision=32, epsilon=0.1, kinetic_variant=0,
-                 use_graph=True, stream=None):
+                 use_graph=True, stream=None, heights=None):
         import torch
         self.lengths = np.asarray(lengths, dtype=np.int64)
+        self.heights = np.ones_like(self.lengths) if heights is None else np.asarray(heights, dtype=np.int64)
         self.nruns = len(self.lengths)
         self.dtype = np.float32 if precision == 32 else np.float64
         cfg, keep = make_batch_config(lengths, couplings, precision, epsilon, kinetic_variant,
-                                      use_graph)
+                                      use_graph, heights)
         if stream is None:
             # graph capture needs a stream other than the legacy default stream
             stream = torch.cuda.Stream() if use_graph else torch.cuda.current_stream()
@@ -620,7 +626,7 @@ class Batch1D:
         _check(load_library().qlga_batch_create(ctypes.byref(cfg), _VP(self.stream.cuda_stream),
                                                 ctypes.byref(h)), "qlga_batch_create")
         self.handle = h.value
-        self.nreals = int(self.lengths.sum()) * 20
+        self.nreals = int((self.lengths * self.heights).sum()) * 20
 
     def load_state(self, state):
         a = np.ascontiguousarray(state, dtype=self.dtype).ravel()
@@ -659,3 +665,6 @@ class Batch1D:
             self.close()
         except Exception:
             pass
+
+
+Batch1D = Batch  # the 1D-only name

@@ -1,4 +1,5 @@
-"""Batches of 1D lattices (uneven lengths, per-run couplings) against the oracle, run by run."""
+"""Batches of lattices (uneven sizes, per-run couplings; 1D runs and 2D runs) against the
+oracle, run by run."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,54 @@ def test_config3_full_batch_sampled_runs():
         assert rel_l2(runs[r], ref) <= 2e-5, r
     for a, c in zip(o0, o1):
         assert abs(c["norm_qubit"] - a["norm_qubit"]) <= 1e-5 * a["norm_qubit"]
+
+
+# (nx, ny): 1D runs have ny = 1; 2D runs need nx a multiple of 32 (ragged row chunks, a single
+# strip whose halo wraps onto itself at nx = 32)
+SHAPES = [(100, 1), (64, 40), (37, 1), (96, 33), (32, 17), (128, 64), (8, 1)]
+
+
+def split_shapes(state, shapes):
+    out, o = [], 0
+    for nx, ny in shapes:
+        out.append(np.asarray(state[o:o + 20 * nx * ny]).reshape(5, ny, nx, 2, 2))
+        o += 20 * nx * ny
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_mixed_1d_2d_batch_matches_oracle_per_run(use_graph, variant):
+    rng = np.random.default_rng(71 + variant)
+    n_runs = len(SHAPES)
+    couplings = np.column_stack([np.ones(n_runs), rng.uniform(-1, 1, n_runs), rng.uniform(-1, 1, n_runs)])
+    state = np.concatenate([I.random_state(rng, nx, ny, scale=0.05).ravel() for nx, ny in SHAPES])
+    state = state.astype(np.float32)
+    lengths = [nx for nx, _ in SHAPES]
+    heights = [ny for _, ny in SHAPES]
+    b = qlga.Batch(lengths, couplings, precision=32, kinetic_variant=variant, use_graph=use_graph,
+                   heights=heights)
+    b.load_state(state)
+    n = 13
+    b.step(n)
+    got = split_shapes(b.get_state(), SHAPES)
+    obs = b.observables()
+    b.close()
+    for st, (nx, ny), g, gr, ob in zip(split_shapes(state, SHAPES), SHAPES, couplings, got, obs):
+        ndim = 1 if ny == 1 else 2
+        cfg = oracle.make_cfg(ndim, nx, ny, *g, kinetic_variant=variant)
+        ref = np.ascontiguousarray(st, dtype=np.float64).copy()
+        oracle.step(ref, cfg, n)
+        assert rel_l2(gr, ref) <= 2e-5, (nx, ny)
+        ro = oracle.observables(ref, cfg)
+        assert abs(ob["energy"] - ro["energy"]) <= 1e-5 * abs(ro["energy"]), (nx, ny)
+        assert abs(ob["norm_qubit"] - ro["norm_qubit"]) <= 1e-6 * ro["norm_qubit"]
+
+
+def test_2d_batch_rejects_unsupported_runs():
+    with pytest.raises(qlga.QlgaError) as e:
+        qlga.Batch([64, 100], [[1, 0.1, 0.2]] * 2, precision=64, heights=[16, 1])
+    assert e.value.status == qlga.QLGA_ERR_UNSUPPORTED
+    with pytest.raises(qlga.QlgaError) as e:
+        qlga.Batch([40], [[1, 0.1, 0.2]], precision=32, heights=[16])
+    assert e.value.status == qlga.QLGA_ERR_INVALID_ARG

@@ -458,7 +458,10 @@ def run_e2e(lat, state, args, torch, qlga, sites):
     return {"value": sites * args.steps / dt, "unit": UNIT, "seconds": dt,
             "h2d_bytes_per_step": nbytes / args.steps,
             "d2h_bytes_per_step": (nbytes + 8 * 16 * (args.steps // max(args.obs_every, 1))) / args.steps,
-            "note": "includes %d warm-up steps after the upload" % args.warmup}
+            "note": "the simulation's input is its state: uploaded once from pinned host memory, "
+                    "%d warm-up and %d timed steps, observables read back every %d steps, the final "
+                    "state read back to pinned memory; bytes per step = those transfers / timed steps"
+                    % (args.warmup, args.steps, args.obs_every)}
 
 
 # ----------------------------------------------------------------------------- reference arm

@@ -31,6 +31,7 @@
 #include "qlga_batch1d.cuh"
 #include "qlga_adjoint.cuh"
 #include "qlga_interleave.cuh"
+#include "qlga_step2d_f64.cuh"
 
 #include <vector>
 
@@ -509,7 +510,7 @@ inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm) {
 // Per-device launch facts (SM count, resident warp strips per SM), set up once per device.  The
 // shared-memory opt-in is a per-device function attribute, so it is applied on each device.
 struct Step2dDevice {
-    int sms = 0, per_sm = 0;
+    int sms = 0, per_sm = 0, per_sm64 = 0;
 };
 
 inline int step2d_device(Step2dDevice* out) {
@@ -535,10 +536,39 @@ inline int step2d_device(Step2dDevice* out) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_step2d_f32<0, true>, kStep2dWarpsPerCta * 32, smem) != cudaSuccess)
             return 1;
         d.per_sm = ctas > 0 ? ctas * kStep2dWarpsPerCta : 1;
+        const int s64 = kStep2d64SmemBytes;
+        if (cudaFuncSetAttribute(k_step2d_f64<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f64<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f64<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_step2d_f64<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64) != cudaSuccess) return 1;
+        int ctas64 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas64, k_step2d_f64<0, true>, kStep2d64WarpsPerCta * 32, s64) != cudaSuccess)
+            return 1;
+        d.per_sm64 = ctas64 > 0 ? ctas64 * kStep2d64WarpsPerCta : 1;
         d.sms = sms;
     }
     *out = d;
     return 0;
+}
+
+// FP64 form (qlga_step2d_f64.cuh); same contract as step2d_f32_launch.
+inline int step2d_f64_launch(const double* in, double* out, int64_t nx, int64_t ny, int variant, bool pot,
+                             PotConst<double> PC, unsigned* status, cudaStream_t stream) {
+    Step2dDevice dv;
+    if (step2d_device(&dv)) return 1;
+    const int64_t strips = nx / kStep2dWarpCols;
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64);
+    const int grid = int((strips * chunks + kStep2d64WarpsPerCta - 1) / kStep2d64WarpsPerCta);
+    const dim3 b(kStep2d64WarpsPerCta * 32);
+    const int smem = kStep2d64SmemBytes;
+    if (variant == 0) {
+        if (pot) k_step2d_f64<0, true><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f64<0, false><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    } else {
+        if (pot) k_step2d_f64<1, true><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+        else k_step2d_f64<1, false><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
+    }
+    return cudaPeekAtLastError() != cudaSuccess;
 }
 
 // Returns 0 on success (errors are left in cudaGetLastError()).  pot = false applies the kinetic
@@ -830,11 +860,15 @@ qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot) {
 // x pass.  With pot, U follows the last axis (the fused step).
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
     if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
-    if (h->cfg.precision == 32 && step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
-        if (step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx,
-                              h->cfg.ny, h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)),
-                              h->status, h->stream))
-            return cuda_fail(cudaGetLastError(), "step2d launch");
+    if (step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
+        const int err = h->cfg.precision == 32
+            ? step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny,
+                                h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)), h->status,
+                                h->stream)
+            : step2d_f64_launch(static_cast<const double*>(in), static_cast<double*>(out), h->cfg.nx, h->cfg.ny,
+                                h->cfg.kinetic_variant, pot, PotConst<double>(pot_params(h->cfg, 1.0)), h->status,
+                                h->stream);
+        if (err) return cuda_fail(cudaGetLastError(), "step2d launch");
         h->launches += 1;
         return QLGA_OK;
     }

@@ -123,6 +123,19 @@ def test_steps_fp32_fused_2d(nx, ny, variant):
     assert rel_l2(got, ref) <= 1e-5
 
 
+# the fused FP64 2D kernel (warp strips, nx a multiple of 32)
+@pytest.mark.parametrize("nx,ny", [(32, 8), (96, 13), (128, 41), (256, 67)])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_steps_fp64_fused_2d(nx, ny, variant):
+    rng = np.random.default_rng(97 + nx + ny)
+    st = I.random_state(rng, nx, ny, scale=0.05)
+    g = G_SETS[1]
+    n = 12
+    got = run_gpu(st, 2, nx, ny, g, n, 64, variant=variant)
+    ref = run_oracle(st, 2, nx, ny, g, n, variant=variant)
+    assert rel_l2(got, ref) <= 1e-11
+
+
 @pytest.mark.parametrize("ndim,nx,ny,variant", [(1, 64, 1, 0), (2, 24, 20, 0), (1, 131, 1, 1),
                                                  (2, 130, 37, 1), (2, 250, 9, 0), (1, 8, 1, 0)])
 @pytest.mark.parametrize("precision", [64, 32])

@@ -498,13 +498,35 @@ inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
            ny <= (int64_t(1) << 30);
 }
 
-// Row chunks per strip so that the grid fills every SM once at the kernel's occupancy (per_sm
-// resident warp strips per SM).
-inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm) {
-    int64_t chunks = (int64_t(sms) * per_sm) / strips;
-    if (chunks < 1) chunks = 1;
-    if (chunks > ny) chunks = ny;
-    return int(chunks);
+// Row chunks per strip.  A chunk of r rows costs about r + 3.2 row updates: its first 8 rows only
+// fill the y pipeline (kinetic work, ~0.4 of a row each).  `fill` is the number of warps per SM
+// that keeps the limiting pipe busy (FP32: every resident warp; FP64: one per SM sub-partition,
+// since one FP64 FMA of a warp holds the FP64 pipe for many cycles).  With W = strips x chunks
+// warps the step takes about ceil(W / (sms x fill)) x (ceil(ny / chunks) + 3.2) row times; the
+// chunk count that minimises this, up to the resident capacity sms x per_sm, is used (the larger
+// on ties).
+inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fill) {
+    int64_t cmax = (int64_t(sms) * per_sm) / strips;
+    if (cmax > ny) cmax = ny;
+    if (cmax <= 1) return 1;
+    const int64_t lanes = int64_t(sms) * (fill < 1 ? 1 : fill);
+    // within one wave count the cost falls with the chunk count, so only the largest chunk count
+    // of each wave count is a candidate: c_k = min(cmax, k lanes / strips), k = 1, 2, ...
+    int64_t best = 1, best_cost = -1;
+    for (int64_t k = 1;; ++k) {
+        int64_t c = (k * lanes) / strips;
+        if (c > cmax) c = cmax;
+        if (c >= 1) {
+            const int64_t waves = (strips * c + lanes - 1) / lanes;
+            const int64_t cost = waves * (10 * ((ny + c - 1) / c) + 32);  // row times x 10
+            if (best_cost < 0 || cost <= best_cost) {
+                best = c;
+                best_cost = cost;
+            }
+        }
+        if (c >= cmax) break;
+    }
+    return int(best);
 }
 
 // Per-device launch facts (SM count, resident warp strips per SM), set up once per device.  The
@@ -557,7 +579,7 @@ inline int step2d_f64_launch(const double* in, double* out, int64_t nx, int64_t 
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4);
     const int grid = int((strips * chunks + kStep2d64WarpsPerCta - 1) / kStep2d64WarpsPerCta);
     const dim3 b(kStep2d64WarpsPerCta * 32);
     const int smem = kStep2d64SmemBytes;
@@ -578,7 +600,7 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm, dv.per_sm);
     const int grid = int((strips * chunks + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta);
     const dim3 b(kStep2dWarpsPerCta * 32);
     const int smem = kStep2dWarpSmemBytes;

@@ -151,18 +151,46 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n):
-    """DRAM bytes per launch of the fused step kernel from the committed ncu summary, scaled to an
-    n x n lattice; None when the summary is missing or the kernel source changed since."""
+def recorded_step_counters():
+    """The committed ncu figures of the fused step kernel (per site), or None when the summary is
+    missing or the kernel source changed since the capture."""
     path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    return float(d["dram_bytes_per_site"]) * n * n
+    return d if d.get("kernel_source_hash") == kernel_source_hash() else None
+
+
+def alu_roofline(sites, kernel_ms, sms):
+    """FP32 FMA-pipe view of the fused step: issue cycles per site from the ncu capture, over the
+    live launch duration, against one FMA-pipe issue per SM sub-partition per cycle at the maximum
+    SM clock (4 sub-partitions per SM)."""
+    d = recorded_step_counters()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        mhz, src = 2070.0, "nominal 2070 MHz"
+    peak = 4.0 * sms * mhz * 1e6
+    if d is None or "fma_pipe_cycles_per_site" not in d:
+        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "FMA-pipe issue cycles/s",
+                "frac": None, "note": "no ncu figure for the current kernel source"}
+    per_site = float(d["fma_pipe_cycles_per_site"])
+    achieved = per_site * sites / (kernel_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FMA-pipe issue cycles/s",
+            "frac": achieved / peak, "cycles_per_site": per_site,
+            "peak_source": "4 sub-partitions x %d SMs x %s" % (sms, src),
+            "note": "FP32 FMA-pipe issue cycles per site from ncu on the settled 2048^2 state "
+                    "(profiles/step2d_f32_2048_full.md); the pipe, not HBM, bounds the fused step"}
+
+
+def recorded_traffic(n):
+    """DRAM bytes per launch of the fused step kernel from the committed ncu summary, scaled to an
+    n x n lattice; None when the summary is missing or the kernel source changed since."""
+    d = recorded_step_counters()
+    return None if d is None else float(d["dram_bytes_per_site"]) * n * n
 
 
 def cpu_baseline(state_f64, g, budget_s, n_sub=256):
@@ -296,6 +324,7 @@ def run_gb300(args):
                      "note": "the fused step is limited by FP32 FMA-pipe cycles of the potential "
                              "(ncu on the settled state: FMA pipe 61% busy, DRAM 36%; "
                              "profiles/step2d_f32_2048_full.md), not by HBM traffic"},
+        "alu": alu_roofline(sites, kernel_ms, torch.cuda.get_device_properties(0).multi_processor_count),
         "e2e": e2e,
         "drift": drift,
         "gpu_launches": launches,

@@ -62,3 +62,16 @@ def test_reference_arm_other_ranks_do_no_work():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_recorded_counters_follow_the_kernel_source(monkeypatch):
+    """The ncu per-site figures apply only to the kernel source they were taken on."""
+    d = bench.recorded_step_counters()
+    assert d is not None and d["kernel_source_hash"] == bench.kernel_source_hash()
+    a = bench.alu_roofline(4096 * 4096, 0.9, 152)
+    assert a["bound"] == "alu" and 0 < a["frac"] < 1.2
+    assert a["frac"] == pytest.approx(d["fma_pipe_cycles_per_site"] * 4096 * 4096 / 0.9e-3 / a["peak"])
+    assert bench.recorded_traffic(4096) == pytest.approx(d["dram_bytes_per_site"] * 4096 * 4096)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.recorded_traffic(4096) is None
+    assert bench.alu_roofline(4096 * 4096, 0.9, 152)["frac"] is None

@@ -190,6 +190,23 @@ qlga_status qlga_observables_noalloc(const qlga_config* cfg, const void* state_d
  * even, 0..4096; 0 turns graphs off.  Larger lattices start with 0. */
 qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps);
 
+/* Which kernel runs a step on a 2D lattice.  Sec. VII.B's step is the same either way; the two
+ * forms differ only in how the passes are grouped, and their results agree to rounding.
+ *   QLGA_STEP2D_AUTO      (default) the fused single-pass kernel when nx is a multiple of 32 and,
+ *                         in FP64, a cost estimate favours it (on small FP64 lattices each row
+ *                         chunk's warm-up rows outweigh the saved pass);
+ *   QLGA_STEP2D_FUSED     always the fused kernel (warp strips of 32 columns: nx % 32 == 0);
+ *   QLGA_STEP2D_TWO_PASS  always two passes: x, then y with the potential.
+ * Errors: QLGA_ERR_INVALID_ARG for an unknown mode, QLGA_ERR_UNSUPPORTED for QLGA_STEP2D_FUSED
+ * on a 1D lattice or nx not a multiple of 32.  Changing the mode waits for the handle's stream
+ * and drops captured step graphs.  qlga_get_step2d_kernel() reports the form the next step uses
+ * (QLGA_STEP2D_FUSED or QLGA_STEP2D_TWO_PASS; 0 on a 1D lattice). */
+#define QLGA_STEP2D_AUTO 0
+#define QLGA_STEP2D_FUSED 1
+#define QLGA_STEP2D_TWO_PASS 2
+qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode);
+qlga_status qlga_get_step2d_kernel(qlga_handle* h, int32_t* kernel);
+
 /* Number of kernels this handle has launched since creation (a diagnostic for benchmarks). */
 qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count);
 

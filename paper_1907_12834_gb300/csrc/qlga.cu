@@ -498,14 +498,15 @@ inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
            ny <= (int64_t(1) << 30);
 }
 
-// Row chunks per strip.  A chunk of r rows costs about r + 3.2 row updates: its first 8 rows only
-// fill the y pipeline (kinetic work, ~0.4 of a row each).  `fill` is the number of warps per SM
-// that keeps the limiting pipe busy (FP32: every resident warp; FP64: one per SM sub-partition,
-// since one FP64 FMA of a warp holds the FP64 pipe for many cycles).  With W = strips x chunks
-// warps the step takes about ceil(W / (sms x fill)) x (ceil(ny / chunks) + 3.2) row times; the
-// chunk count that minimises this, up to the resident capacity sms x per_sm, is used (the larger
-// on ties).
-inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fill) {
+// Row chunks per strip.  A chunk of r rows costs about r + w row updates: its first 8 rows only
+// fill the y pipeline and run the kinetic part of a row update, w = 8 x that part (warm10 = 10 w:
+// 32 in FP32, where the kinetic part is ~0.4 of a row update; 18 in FP64, where it is ~0.23).
+// `fill` is the number of warps per SM that keeps the limiting pipe busy (FP32: every resident
+// warp; FP64: one per SM sub-partition, since one FP64 FMA of a warp holds the FP64 pipe for many
+// cycles).  With W = strips x chunks warps the step takes about ceil(W / (sms x fill)) x
+// (ceil(ny / chunks) + w) row times; the chunk count that minimises this, up to the resident
+// capacity sms x per_sm, is used (the larger on ties).
+inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fill, int warm10) {
     int64_t cmax = (int64_t(sms) * per_sm) / strips;
     if (cmax > ny) cmax = ny;
     if (cmax <= 1) return 1;
@@ -518,7 +519,7 @@ inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fi
         if (c > cmax) c = cmax;
         if (c >= 1) {
             const int64_t waves = (strips * c + lanes - 1) / lanes;
-            const int64_t cost = waves * (10 * ((ny + c - 1) / c) + 32);  // row times x 10
+            const int64_t cost = waves * (10 * ((ny + c - 1) / c) + warm10);  // row times x 10
             if (best_cost < 0 || cost <= best_cost) {
                 best = c;
                 best_cost = cost;
@@ -573,13 +574,30 @@ inline int step2d_device(Step2dDevice* out) {
     return 0;
 }
 
+// FP64: whether the fused kernel beats the two-pass form (x pass, then y pass + U) on an nx x ny
+// lattice (nx a multiple of 32).  The fused kernel costs the row-chunk estimate above; the
+// two-pass form has no warm-up rows but evaluates the y axis as a second nine-point stencil and
+// reads and writes the state twice: 1.135 fused row updates per row of a strip, spread over all
+// sub-partitions (calibrated on 4096^2, 56.0 vs 52.4 ms per step).  Short chunks on small lattices
+// favour the two-pass form (512^2: 0.93 vs 0.99 ms per step; 384 x 107: 0.21 vs 0.35 ms).
+inline bool step2d_f64_fused_preferred(int64_t nx, int64_t ny) {
+    Step2dDevice dv;
+    if (step2d_device(&dv)) return true;  // the launch reports the error
+    const int64_t strips = nx / kStep2dWarpCols;
+    const int64_t c = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4, 18);
+    const int64_t lanes = 4 * int64_t(dv.sms);
+    const double fused = double((strips * c + lanes - 1) / lanes) * (double((ny + c - 1) / c) + 1.8);
+    const double two_pass = 1.135 * double(strips * ny) / double(lanes);
+    return fused <= two_pass;
+}
+
 // FP64 form (qlga_step2d_f64.cuh); same contract as step2d_f32_launch.
 inline int step2d_f64_launch(const double* in, double* out, int64_t nx, int64_t ny, int variant, bool pot,
                              PotConst<double> PC, unsigned* status, cudaStream_t stream) {
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4, 18);
     const int grid = int((strips * chunks + kStep2d64WarpsPerCta - 1) / kStep2d64WarpsPerCta);
     const dim3 b(kStep2d64WarpsPerCta * 32);
     const int smem = kStep2d64SmemBytes;
@@ -600,7 +618,7 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm, dv.per_sm);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm, dv.per_sm, 32);
     const int grid = int((strips * chunks + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta);
     const dim3 b(kStep2dWarpsPerCta * 32);
     const int smem = kStep2dWarpSmemBytes;
@@ -702,6 +720,7 @@ struct qlga_handle {
     int64_t step;
     int64_t launches;  // kernels launched by this handle
     int tile_cand;  // 1D: launch shape of the tiled step (index into kBatchCands), -1 untuned
+    int step2d_mode;  // QLGA_STEP2D_AUTO / _FUSED / _TWO_PASS
     // CUDA graphs of graph_steps fused steps starting (and ending) on buffer 0 or 1
     int graph_steps;
     int64_t graph_launches;  // kernels in one graph
@@ -880,9 +899,17 @@ qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot) {
 
 // Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
 // x pass.  With pot, U follows the last axis (the fused step).
+// The 2D kernel form of this handle's steps (see qlga_set_step2d_mode).
+bool step2d_uses_fused(const qlga_handle* h) {
+    if (h->cfg.ndim != 2 || !step2d_f32_supported(h->cfg.nx, h->cfg.ny)) return false;
+    if (h->step2d_mode == QLGA_STEP2D_FUSED) return true;
+    if (h->step2d_mode == QLGA_STEP2D_TWO_PASS) return false;
+    return h->cfg.precision == 32 || step2d_f64_fused_preferred(h->cfg.nx, h->cfg.ny);
+}
+
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
     if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
-    if (step2d_f32_supported(h->cfg.nx, h->cfg.ny)) {
+    if (step2d_uses_fused(h)) {
         const int err = h->cfg.precision == 32
             ? step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny,
                                 h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)), h->status,
@@ -1137,6 +1164,7 @@ static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* str
     h->graph_launches = 0;
     h->graph[0] = h->graph[1] = nullptr;
     h->tile_cand = -1;
+    h->step2d_mode = QLGA_STEP2D_AUTO;
     QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
     QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
     return QLGA_OK;
@@ -1382,6 +1410,24 @@ qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps) {
     cudaStreamSynchronize(h->stream);
     graphs_release(h);
     h->graph_steps = steps;
+    return QLGA_OK;
+}
+
+qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    if (mode != QLGA_STEP2D_AUTO && mode != QLGA_STEP2D_FUSED && mode != QLGA_STEP2D_TWO_PASS)
+        return fail(QLGA_ERR_INVALID_ARG, "mode must be QLGA_STEP2D_AUTO, _FUSED or _TWO_PASS%s");
+    if (mode == QLGA_STEP2D_FUSED && (h->cfg.ndim != 2 || !step2d_f32_supported(h->cfg.nx, h->cfg.ny)))
+        return fail(QLGA_ERR_UNSUPPORTED, "the fused 2D kernel needs a 2D lattice with nx a multiple of 32%s");
+    cudaStreamSynchronize(h->stream);
+    graphs_release(h);
+    h->step2d_mode = mode;
+    return QLGA_OK;
+}
+
+qlga_status qlga_get_step2d_kernel(qlga_handle* h, int32_t* kernel) {
+    if (!h || !kernel) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    *kernel = h->cfg.ndim != 2 ? 0 : (step2d_uses_fused(h) ? QLGA_STEP2D_FUSED : QLGA_STEP2D_TWO_PASS);
     return QLGA_OK;
 }
 

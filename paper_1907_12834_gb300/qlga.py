@@ -21,6 +21,7 @@ QLGA_OK, QLGA_ERR_INVALID_ARG, QLGA_ERR_OOM, QLGA_ERR_CUDA, QLGA_ERR_TIMEOUT, \
     QLGA_ERR_NOT_FINITE, QLGA_ERR_UNSUPPORTED = range(7)
 QLGA_HOST, QLGA_DEVICE = 0, 1
 QLGA_KINETIC_K1, QLGA_KINETIC_K2 = 0, 1
+QLGA_STEP2D_AUTO, QLGA_STEP2D_FUSED, QLGA_STEP2D_TWO_PASS = 0, 1, 2
 
 
 class QlgaConfig(ctypes.Structure):
@@ -78,6 +79,8 @@ _SIGNATURES = {
     "qlga_synchronize": [_H],
     "qlga_launch_count": [_H, ctypes.POINTER(ctypes.c_int64)],
     "qlga_set_graph_steps": [_H, ctypes.c_int32],
+    "qlga_set_step2d_mode": [_H, ctypes.c_int32],
+    "qlga_get_step2d_kernel": [_H, ctypes.POINTER(ctypes.c_int32)],
     "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_fields": [_H, _VP, ctypes.c_int],
     "qlga_batch_state_bytes": [ctypes.POINTER(QlgaBatchConfig), ctypes.POINTER(ctypes.c_size_t)],
@@ -231,6 +234,16 @@ def qlga_launch_count(h: int) -> int:
 
 def qlga_set_graph_steps(h: int, steps: int):
     _check(load_library().qlga_set_graph_steps(_H(h), ctypes.c_int32(int(steps))), "qlga_set_graph_steps")
+
+
+def qlga_set_step2d_mode(h: int, mode: int):
+    _check(load_library().qlga_set_step2d_mode(_H(h), ctypes.c_int32(int(mode))), "qlga_set_step2d_mode")
+
+
+def qlga_get_step2d_kernel(h: int) -> int:
+    out = ctypes.c_int32()
+    _check(load_library().qlga_get_step2d_kernel(_H(h), ctypes.byref(out)), "qlga_get_step2d_kernel")
+    return out.value
 
 
 def qlga_synchronize(h: int):
@@ -427,6 +440,14 @@ class Lattice:
         ws = self.adjoint_workspace(nsteps, checkpoint_every)
         self.adjoint_forward(x0, nsteps, checkpoint_every, ws)
         return self.adjoint_backward(cot, nsteps, checkpoint_every, ws)
+
+    def set_step2d_mode(self, mode):
+        """2D kernel form: QLGA_STEP2D_AUTO (default), QLGA_STEP2D_FUSED or QLGA_STEP2D_TWO_PASS."""
+        qlga_set_step2d_mode(self.handle, mode)
+
+    def step2d_kernel(self):
+        """The 2D kernel form the next step uses (QLGA_STEP2D_FUSED / _TWO_PASS; 0 in 1D)."""
+        return qlga_get_step2d_kernel(self.handle)
 
     def set_graph_steps(self, steps):
         """Steps per CUDA graph replay (even; 0 turns graphs off)."""

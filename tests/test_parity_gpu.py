@@ -25,9 +25,12 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def run_gpu(state, ndim, nx, ny, g, nsteps, precision=64, interleave=0, variant=0):
+def run_gpu(state, ndim, nx, ny, g, nsteps, precision=64, interleave=0, variant=0, step2d_mode=None):
     lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=g, interleave=interleave,
                        kinetic_variant=variant)
+    if step2d_mode is not None:
+        lat.set_step2d_mode(step2d_mode)
+        assert lat.step2d_kernel() == step2d_mode
     lat.load_state(state.astype(np.float32 if precision == 32 else np.float64))
     lat.step(nsteps)
     out = lat.get_state()
@@ -123,17 +126,53 @@ def test_steps_fp32_fused_2d(nx, ny, variant):
     assert rel_l2(got, ref) <= 1e-5
 
 
-# the fused FP64 2D kernel (warp strips, nx a multiple of 32)
+# both 2D kernel forms on lattices the fused kernel takes (nx a multiple of 32): the fused FP64
+# warp-strip kernel, and the two-pass form that small FP64 lattices use by default
 @pytest.mark.parametrize("nx,ny", [(32, 8), (96, 13), (128, 41), (256, 67)])
 @pytest.mark.parametrize("variant", [0, 1])
-def test_steps_fp64_fused_2d(nx, ny, variant):
+@pytest.mark.parametrize("mode", [qlga.QLGA_STEP2D_FUSED, qlga.QLGA_STEP2D_TWO_PASS])
+def test_steps_fp64_fused_2d(nx, ny, variant, mode):
     rng = np.random.default_rng(97 + nx + ny)
     st = I.random_state(rng, nx, ny, scale=0.05)
     g = G_SETS[1]
     n = 12
-    got = run_gpu(st, 2, nx, ny, g, n, 64, variant=variant)
+    got = run_gpu(st, 2, nx, ny, g, n, 64, variant=variant, step2d_mode=mode)
     ref = run_oracle(st, 2, nx, ny, g, n, variant=variant)
     assert rel_l2(got, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 9), (256, 67)])
+def test_steps_fp32_two_pass_on_fused_shapes(nx, ny):
+    rng = np.random.default_rng(29 + nx + ny)
+    st = I.random_state(rng, nx, ny, scale=0.05).astype(np.float32)
+    got = run_gpu(st, 2, nx, ny, G_SETS[2], 12, 32, step2d_mode=qlga.QLGA_STEP2D_TWO_PASS)
+    ref = run_oracle(st, 2, nx, ny, G_SETS[2], 12)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_step2d_mode_choice_and_errors():
+    def kernel(ndim, nx, ny, precision, mode=None):
+        lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=G_SETS[2])
+        try:
+            if mode is not None:
+                lat.set_step2d_mode(mode)
+            return lat.step2d_kernel()
+        finally:
+            lat.close()
+    assert kernel(1, 64, 1, 64) == 0
+    assert kernel(2, 40, 16, 32) == qlga.QLGA_STEP2D_TWO_PASS        # nx not a multiple of 32
+    assert kernel(2, 64, 16, 32) == qlga.QLGA_STEP2D_FUSED           # FP32 default
+    assert kernel(2, 64, 16, 64, qlga.QLGA_STEP2D_TWO_PASS) == qlga.QLGA_STEP2D_TWO_PASS
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        # FP64 default on GB300: short row chunks favour two passes, long ones the fused kernel
+        assert kernel(2, 384, 107, 64) == qlga.QLGA_STEP2D_TWO_PASS
+        assert kernel(2, 2048, 2048, 64) == qlga.QLGA_STEP2D_FUSED
+    for args, status in (((2, 40, 16, 32, qlga.QLGA_STEP2D_FUSED), qlga.QLGA_ERR_UNSUPPORTED),
+                         ((1, 64, 1, 64, qlga.QLGA_STEP2D_FUSED), qlga.QLGA_ERR_UNSUPPORTED),
+                         ((2, 64, 16, 32, 7), qlga.QLGA_ERR_INVALID_ARG)):
+        with pytest.raises(qlga.QlgaError) as e:
+            kernel(*args)
+        assert e.value.status == status
 
 
 @pytest.mark.parametrize("ndim,nx,ny,variant", [(1, 64, 1, 0), (2, 24, 20, 0), (1, 131, 1, 1),

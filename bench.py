@@ -468,29 +468,37 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     return out
 
 
+E2E_REPEATS = 3
+
+
 def run_e2e(lat, state, args, torch, qlga, sites):
     """Same steps through the C ABI with host buffers: pinned upload of the (settled) state,
-    steps, observables, pinned read-back of the final state, all inside the timed region."""
+    steps, observables, pinned read-back of the final state, all inside the timed region.  The
+    pinned copies share the host's memory with other work on the machine, so the run is made
+    E2E_REPEATS times and the median time is reported (all of them are listed)."""
     host_in = torch.from_numpy(state).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    qlga.qlga_load_state(lat.handle, host_in.data_ptr(), qlga.QLGA_HOST)
-    qlga.qlga_step(lat.handle, args.warmup)
-    for i in range(args.steps):
-        qlga.qlga_step(lat.handle, 1)
-        if args.obs_every and (i + 1) % args.obs_every == 0:
-            qlga.qlga_observables(lat.handle)
-    qlga.qlga_get_state(lat.handle, host_out.data_ptr(), qlga.QLGA_HOST)
-    dt = time.perf_counter() - t0
+    times = []
+    for _ in range(E2E_REPEATS):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qlga.qlga_load_state(lat.handle, host_in.data_ptr(), qlga.QLGA_HOST)
+        for i in range(args.steps):
+            qlga.qlga_step(lat.handle, 1)
+            if args.obs_every and (i + 1) % args.obs_every == 0:
+                qlga.qlga_observables(lat.handle)
+        qlga.qlga_get_state(lat.handle, host_out.data_ptr(), qlga.QLGA_HOST)
+        times.append(time.perf_counter() - t0)
+    dt = sorted(times)[len(times) // 2]
     nbytes = host_in.numel() * host_in.element_size()
     return {"value": sites * args.steps / dt, "unit": UNIT, "seconds": dt,
+            "repeats": [sites * args.steps / t for t in times],
             "h2d_bytes_per_step": nbytes / args.steps,
             "d2h_bytes_per_step": (nbytes + 8 * 16 * (args.steps // max(args.obs_every, 1))) / args.steps,
             "note": "the simulation's input is its state: uploaded once from pinned host memory, "
-                    "%d warm-up and %d timed steps, observables read back every %d steps, the final "
-                    "state read back to pinned memory; bytes per step = those transfers / timed steps"
-                    % (args.warmup, args.steps, args.obs_every)}
+                    "%d steps with the observables read back every %d steps, the final state read "
+                    "back to pinned memory; bytes per step = those transfers / steps; median of %d "
+                    "runs (repeats)" % (args.steps, args.obs_every, E2E_REPEATS)}
 
 
 # ----------------------------------------------------------------------------- reference arm

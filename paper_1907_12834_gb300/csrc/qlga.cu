@@ -27,11 +27,13 @@
 #include <type_traits>
 
 #include "qlga_device.cuh"
+#include "qlga_obs.cuh"
 #include "qlga_step2d.cuh"
 #include "qlga_batch1d.cuh"
 #include "qlga_adjoint.cuh"
 #include "qlga_interleave.cuh"
 #include "qlga_step2d_f64.cuh"
+#include "qlga_obs2d.cuh"
 
 #include <vector>
 
@@ -73,34 +75,6 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // ===================================================================== kernels
 
 namespace qlga {
-
-template <class T>
-__device__ __forceinline__ void load_pair(const T* X, int64_t nsites, int m, int64_t site,
-                                          cpx<T>& a, cpx<T>& b);
-template <>
-__device__ __forceinline__ void load_pair<float>(const float* X, int64_t nsites, int m,
-                                                 int64_t site, cpx<float>& a, cpx<float>& b) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(X) + m * nsites + site);
-    a = {v.x, v.y};
-    b = {v.w, -v.z};  // resident bt = i b
-}
-template <>
-__device__ __forceinline__ void load_pair<double>(const double* X, int64_t nsites, int m,
-                                                  int64_t site, cpx<double>& a, cpx<double>& b) {
-    const double2* p = reinterpret_cast<const double2*>(X) + 2 * (m * nsites + site);
-    const double2 va = __ldg(p), vb = __ldg(p + 1);
-    a = {va.x, va.y};
-    b = {vb.y, -vb.x};
-}
-
-// Pair load from a buffer in the ABI layout (a.re, a.im, b.re, b.im).
-template <class T>
-__device__ __forceinline__ void load_pair_abi(const T* X, int64_t nsites, int m, int64_t site,
-                                              cpx<T>& a, cpx<T>& b) {
-    const T* p = X + 4 * (m * nsites + site);
-    a = {p[0], p[1]};
-    b = {p[2], p[3]};
-}
 
 // ABI layout <-> resident layout, one (a, b) pair per thread; safe in place.
 template <class T, bool TO_RESIDENT>
@@ -207,34 +181,6 @@ __global__ void k_load_boson(const T* __restrict__ psi5, T* __restrict__ X, int6
     }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Per-thread accumulator: FP64 for an FP64 state; compensated (Kahan) FP32 for an FP32 state,
-// whose per-site terms carry FP32 rounding anyway.  Block and grid sums are FP64.
-template <class T>
-struct ThreadSum;
-template <>
-struct ThreadSum<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double v) { s += v; }
-    __device__ __forceinline__ double value() const { return s; }
-};
-template <>
-struct ThreadSum<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return double(s) - double(c); }
-};
-
 // Per-site observable terms in the state's precision, block sums (FP64) into
 // partials[block][OBS_COUNT].  X_RESIDENT: X is in the resident layout (else the ABI layout);
 // the reference state is always a caller buffer in the ABI layout.
@@ -246,7 +192,6 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
                                                           double* __restrict__ partials) {
     const int64_t nsites = nx * ny;
     ThreadSum<T> acc[OBS_COUNT];
-    const T r32 = T(1.2247448713915890491);
     const T hg0 = T(0.5 * g0), hg1 = T(0.5 * g1), tg2 = T(0.1 * g2);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
@@ -264,15 +209,9 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
             rho += norm2(psi[m]);
         }
         acc[OBS_NORM_BOSON].add(rho);
-        // F_z, F_+ = psi^dagger f_+ psi (f_+ = f_x + i f_y): |F|^2 = F_z^2 + |F_+|^2
-        const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
-        cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
-        const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
-        Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
-        const T F2 = Fz * Fz + norm2(Fp);
-        // theta = psi^T J psi = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2
-        const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
-        const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+        T F2;
+        cpx<T> th;
+        obs_local(psi, F2, th);
         const T th2 = norm2(th);
         T grad = T(0);
         for (int ax = 0; ax < ndim; ++ax) {
@@ -318,16 +257,6 @@ __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ 
     }
 }
 
-// Neumaier-compensated running sum.
-struct CompSum {
-    double s = 0.0, c = 0.0;
-    __device__ __forceinline__ void add(double v) {
-        const double t = s + v;
-        c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-        s = t;
-    }
-};
-
 // Per-run observables of a batch: one CTA per run; terms in the state's precision (compensated
 // per-thread sums for FP32), FP64 block sums in a fixed order; out[run][OBS_COUNT].
 template <class T>
@@ -338,7 +267,6 @@ __global__ void __launch_bounds__(kThreads) k_batch_observables(const T* __restr
     const BatchRun run = runs[blockIdx.x];
     const int L = run.L;
     const int ny = run.ny, nx = L / ny;
-    const T r32 = T(1.2247448713915890491);
     const T hg0 = T(0.5 * g3[3 * blockIdx.x]), hg1 = T(0.5 * g3[3 * blockIdx.x + 1]);
     const T tg2 = T(0.1 * g3[3 * blockIdx.x + 2]);
     ThreadSum<T> acc[OBS_COUNT];
@@ -359,13 +287,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_observables(const T* __restr
             rho += norm2(psi[m]);
         }
         acc[OBS_NORM_BOSON].add(rho);
-        const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
-        cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
-        const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
-        Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
-        const T F2 = Fz * Fz + norm2(Fp);
-        const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
-        const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+        T F2;
+        cpx<T> th;
+        obs_local(psi, F2, th);
         const T th2 = norm2(th);
         // forward differences along x (and y for a 2D run), periodic within the run
         const int x = j % nx, y = j / nx;
@@ -459,15 +383,18 @@ __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T*
 }
 
 
-// out[k] = compensated sum of partials[b][k] over blocks (rows of ncols), in a fixed order: warp
-// k reduces quantity k, lane l takes blocks l, l+32, ..., then the 32 (sum, compensation) pairs
-// combine in a fixed butterfly.  Launch with ncols warps.
-__global__ void k_reduce_partials(const double* __restrict__ partials, int nblocks, int ncols,
-                                  double* __restrict__ out) {
-    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= ncols) return;
+// out[k] = compensated sum of partials[b][k] over rows b (rows of ncols), in a fixed order: block
+// k reduces quantity k, thread t takes rows t, t + 128, ...; each warp's 32 (sum, compensation)
+// pairs combine in a fixed butterfly, then thread 0 adds the four warps in order.  Launch with
+// ncols blocks of kReduceThreads threads: the FP64 additions of the columns run on ncols SMs.
+constexpr int kReduceThreads = 128;
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_partials(const double* __restrict__ partials,
+                                                                    int nblocks, int ncols,
+                                                                    double* __restrict__ out) {
+    const int k = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (k >= ncols) return;  // whole block
     CompSum cs;
-    for (int b = lane; b < nblocks; b += 32) cs.add(partials[int64_t(b) * ncols + k]);
+    for (int b = threadIdx.x; b < nblocks; b += kReduceThreads) cs.add(partials[int64_t(b) * ncols + k]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double os = __shfl_xor_sync(0xffffffffu, cs.s, o);
@@ -484,7 +411,21 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, int nbloc
         m.c += (lane & o) ? (oc + cs.c) : (cs.c + oc);
         cs = m;
     }
-    if (lane == 0) out[k] = cs.s + cs.c;
+    __shared__ double ws[kReduceThreads / 32], wc[kReduceThreads / 32];
+    if (lane == 0) {
+        ws[w] = cs.s;
+        wc[w] = cs.c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CompSum t;
+        double c = 0.0;
+        for (int i = 0; i < kReduceThreads / 32; ++i) {
+            t.add(ws[i]);
+            c += wc[i];
+        }
+        out[k] = t.s + (t.c + c);
+    }
 }
 
 }  // namespace qlga
@@ -533,7 +474,7 @@ inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fi
 // Per-device launch facts (SM count, resident warp strips per SM), set up once per device.  The
 // shared-memory opt-in is a per-device function attribute, so it is applied on each device.
 struct Step2dDevice {
-    int sms = 0, per_sm = 0, per_sm64 = 0;
+    int sms = 0, per_sm = 0, per_sm64 = 0, per_sm_obs = 0;
 };
 
 inline int step2d_device(Step2dDevice* out) {
@@ -568,6 +509,14 @@ inline int step2d_device(Step2dDevice* out) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas64, k_step2d_f64<0, true>, kStep2d64WarpsPerCta * 32, s64) != cudaSuccess)
             return 1;
         d.per_sm64 = ctas64 > 0 ? ctas64 * kStep2d64WarpsPerCta : 1;
+        if (cudaFuncSetAttribute(k_obs2d_f32<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_obs2d_f32<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_obs2d_f32<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        if (cudaFuncSetAttribute(k_obs2d_f32<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 1;
+        int ctas_obs = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas_obs, k_obs2d_f32<0, true>, kStep2dWarpsPerCta * 32, smem) != cudaSuccess)
+            return 1;
+        d.per_sm_obs = ctas_obs > 0 ? ctas_obs * kStep2dWarpsPerCta : 1;
         d.sms = sms;
     }
     *out = d;
@@ -630,6 +579,59 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
         else k_step2d_f32<1, false><<<grid, b, smem, stream>>>(in, out, int(nx), int(ny), chunks, PC, status);
     }
     return cudaPeekAtLastError() != cudaSuccess;
+}
+
+// Fused observables of a 2D FP32 lattice held pending K (qlga_obs2d.cuh).  Scratch holds the
+// two edge buffers (float2 [strips][ny][5] each) and the partial rows; obs2d_scratch_bytes is its
+// size (at most ~6 bytes per site beside the 80-byte state).
+inline int obs2d_edge_blocks(int64_t strips, int64_t ny) {
+    const int64_t b = (strips * ny + kObs2dEdgeThreads - 1) / kObs2dEdgeThreads;
+    return int(b < 1 ? 1 : (b > kObs2dEdgeBlocksMax ? kObs2dEdgeBlocksMax : b));
+}
+
+inline size_t obs2d_edge_bytes(int64_t nx, int64_t ny) {
+    return (size_t(nx / kStep2dWarpCols) * size_t(ny) * 5 * sizeof(float2) + 255) & ~size_t(255);
+}
+
+inline size_t obs2d_scratch_bytes(int64_t nx, int64_t ny, int warps) {
+    return 2 * obs2d_edge_bytes(nx, ny) +
+           sizeof(double) * OBS_COUNT * size_t(warps + obs2d_edge_blocks(nx / kStep2dWarpCols, ny));
+}
+
+// Launches the read-out; on return partials (inside scratch) holds *rows rows of OBS_COUNT sums.
+// Returns 0 on success, 1 on a launch error (left in cudaGetLastError()), 2 if scratch is too small.
+inline int obs2d_f32_launch(const float* in, const float* ref, int64_t nx, int64_t ny, int variant, double g0,
+                            double g1, double g2, void* scratch, size_t scratch_bytes, cudaStream_t stream,
+                            double** partials, int* rows) {
+    Step2dDevice dv;
+    if (step2d_device(&dv)) return 1;
+    const int64_t strips = nx / kStep2dWarpCols;
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm_obs, dv.per_sm_obs, 32);
+    const int warps = int(strips * chunks);
+    if (obs2d_scratch_bytes(nx, ny, warps) > scratch_bytes) return 2;
+    char* p = static_cast<char*>(scratch);
+    float2* edge_l = reinterpret_cast<float2*>(p);
+    float2* edge_r = reinterpret_cast<float2*>(p + obs2d_edge_bytes(nx, ny));
+    double* part = reinterpret_cast<double*>(p + 2 * obs2d_edge_bytes(nx, ny));
+    const int grid = (warps + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta;
+    const float hg0 = float(0.5 * g0), hg1 = float(0.5 * g1), tg2 = float(0.1 * g2);
+    const dim3 b(kStep2dWarpsPerCta * 32);
+    const int sm = kStep2dWarpSmemBytes;
+    if (variant == 0) {
+        if (ref) k_obs2d_f32<0, true><<<grid, b, sm, stream>>>(in, ref, int(nx), int(ny), chunks, hg0, hg1, tg2, edge_l, edge_r, part);
+        else k_obs2d_f32<0, false><<<grid, b, sm, stream>>>(in, ref, int(nx), int(ny), chunks, hg0, hg1, tg2, edge_l, edge_r, part);
+    } else {
+        if (ref) k_obs2d_f32<1, true><<<grid, b, sm, stream>>>(in, ref, int(nx), int(ny), chunks, hg0, hg1, tg2, edge_l, edge_r, part);
+        else k_obs2d_f32<1, false><<<grid, b, sm, stream>>>(in, ref, int(nx), int(ny), chunks, hg0, hg1, tg2, edge_l, edge_r, part);
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) return 1;
+    const int eb = obs2d_edge_blocks(strips, ny);
+    k_obs2d_edges<<<eb, kObs2dEdgeThreads, 0, stream>>>(edge_l, edge_r, int(strips), int(ny),
+                                                       part + size_t(warps) * OBS_COUNT);
+    if (cudaPeekAtLastError() != cudaSuccess) return 1;
+    *partials = part;
+    *rows = warps + eb;
+    return 0;
 }
 
 }  // namespace qlga
@@ -1097,7 +1099,7 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
                                                            cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
                                                            cfg->g2, scratch);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch (no-alloc)");
-    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, st>>>(scratch, blocks, OBS_COUNT, result);
+    k_reduce_partials<<<OBS_COUNT, kReduceThreads, 0, st>>>(scratch, blocks, OBS_COUNT, result);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (no-alloc)");
     double o[OBS_COUNT];
     QLGA_CUDA(cudaMemcpyAsync(o, result, sizeof(o), cudaMemcpyDeviceToHost, st), "no-alloc observables copy");
@@ -1333,13 +1335,26 @@ qlga_status qlga_apply_kinetic(qlga_handle* h) {
     return QLGA_OK;
 }
 
-qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out) {
-    if (!h || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+// Partial rows of the observable sums of the handle's true state (with the optional reference
+// state for the overlap): *partials, *rows.
+qlga_status observables_partials(qlga_handle* h, const void* ref_state_device, double** partials, int* rows) {
+    if (h->pending_k && h->cfg.precision == 32 && step2d_uses_fused(h)) {
+        // one read of the state: K on the fly in the warp strips, the sums in the same pass; the
+        // work buffer is free between steps and holds the edge fields and partial rows
+        const int err = obs2d_f32_launch(static_cast<const float*>(h->X[h->cur]),
+                                         static_cast<const float*>(ref_state_device), h->cfg.nx, h->cfg.ny,
+                                         h->cfg.kinetic_variant, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->tmp,
+                                         state_bytes_of(h->cfg), h->stream, partials, rows);
+        if (err == 1) return cuda_fail(cudaGetLastError(), "k_obs2d_f32 launch");
+        if (err == 0) {
+            h->launches += 2;
+            return QLGA_OK;
+        }
+    }
     const void* view = nullptr;
     qlga_status s = true_state_view(h, &view);
     if (s != QLGA_OK) return s;
-    const int64_t n = nsites_of(h->cfg);
-    const int blocks = grid_for(n, kObsMaxBlocks);
+    const int blocks = grid_for(nsites_of(h->cfg), kObsMaxBlocks);
     if (h->cfg.precision == 32)
         k_observables<float, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
                                                                  h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
@@ -1347,9 +1362,21 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
         k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
                                                                   h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch");
-    k_reduce_partials<<<1, 32 * OBS_COUNT, 0, h->stream>>>(h->partials, blocks, OBS_COUNT, h->obs_dev);
+    h->launches += 1;
+    *partials = h->partials;
+    *rows = blocks;
+    return QLGA_OK;
+}
+
+qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out) {
+    if (!h || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    double* partials = nullptr;
+    int rows = 0;
+    qlga_status s = observables_partials(h, ref_state_device, &partials, &rows);
+    if (s != QLGA_OK) return s;
+    k_reduce_partials<<<OBS_COUNT, kReduceThreads, 0, h->stream>>>(partials, rows, OBS_COUNT, h->obs_dev);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
-    h->launches += 2;
+    h->launches += 1;
     double o[OBS_COUNT];
     QLGA_CUDA(cudaMemcpyAsync(o, h->obs_dev, sizeof(o), cudaMemcpyDeviceToHost, h->stream), "observables copy");
     QLGA_CUDA(cudaStreamSynchronize(h->stream), "observables sync");
@@ -1570,7 +1597,7 @@ qlga_status adj_pullback(qlga_handle* h, void** cot, void** tmp, const void* xk,
 }
 
 qlga_status adj_finish(qlga_handle* h, const AdjLayout& L, void* cot_res, void* cot_dev, double* dcoup) {
-    k_reduce_partials<<<1, 32 * 3, 0, h->stream>>>(L.partials, kAdjMaxBlocks, 3, L.result);
+    k_reduce_partials<<<3, kReduceThreads, 0, h->stream>>>(L.partials, kAdjMaxBlocks, 3, L.result);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (adjoint)");
     h->launches += 1;
     qlga_status s = launch_convert(h, cot_res, cot_dev, false);

@@ -141,15 +141,17 @@ constexpr int kStep2dWarpsPerCta = 4;
 constexpr int kStep2dWarpSmemBytes =
     kStep2dWarpsPerCta * kStep2dStages * 5 * kStep2dWarpRowSites * 16;
 
-// One warp's work: the strip of columns [x0, x0 + 32) of an nx x ny lattice and output rows
-// [y_begin, y_end); `ring` is the warp's shared-memory ring.
-template <int VARIANT, bool POT, int STYLE>
-__device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float* __restrict__ out, int nx,
-                                             int ny, int x0, int y_begin, int y_end, const PotConst<float>& PC,
-                                             unsigned* status, float4* ring, int lane) {
+// The kinetic operator K on one warp's strip: columns [x0, x0 + 32) of an nx x ny lattice (one
+// column per lane), output rows [y_begin, y_end) in order (y_begin may be -1: rows wrap
+// periodically); `ring` is the warp's shared-memory ring.  For each output row y it calls
+// row_out(y, a, b) with the lane's site of K X as (a, b) pairs, unnormalised: 256 times the true
+// value (the eight collides of the two axes drop their factor 1/2 each).
+template <int VARIANT, int STYLE, class RowOut>
+__device__ __forceinline__ void strip_kinetic_rows(const float* __restrict__ in, int nx, int ny, int x0,
+                                                   int y_begin, int y_end, float4* ring, int lane,
+                                                   RowOut&& row_out) {
     const int64_t nsites = int64_t(nx) * ny;
     const float4* in4 = reinterpret_cast<const float4*>(in);
-    float4* out4 = reinterpret_cast<float4*>(out);
 
     const int nrows = (y_end - y_begin) + 8;
     // ring column r holds lattice column x0 - 4 + r (periodic); lane l stages r = l and, for
@@ -185,9 +187,6 @@ __device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float
 #pragma unroll
         for (int k = 0; k < 4; ++k) st[m][k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
-    const float inv_sigma2 = 1.0f / 65536.0f;
-    const float out_scale = 0.5f / 256.0f;
-
     for (int r = 0; r < nrows; ++r) {
         cp_async_wait<kStep2dStages - 2>();
         __syncwarp();
@@ -219,9 +218,23 @@ __device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float
             oa[m] = {xa.x, xa.y};
             ob[m] = {xbt.y, -xbt.x};
         }
-        if (r >= 8) {
+        if (r >= 8) row_out(y_begin + r - 8, oa, ob);  // pipeline full: output row y_begin + r - 8
+    }
+    cp_async_wait<0>();
+}
+
+// One warp's share of a step: K on the strip, then (POT) the potential unitary, and the store of
+// rows [y_begin, y_end) in the resident layout.  POT = false stores K X alone.
+template <int VARIANT, bool POT, int STYLE>
+__device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float* __restrict__ out, int nx,
+                                             int ny, int x0, int y_begin, int y_end, const PotConst<float>& PC,
+                                             unsigned* status, float4* ring, int lane) {
+    const int64_t nsites = int64_t(nx) * ny;
+    float4* out4 = reinterpret_cast<float4*>(out);
+    strip_kinetic_rows<VARIANT, STYLE>(
+        in, nx, ny, x0, y_begin, y_end, ring, lane, [&](int y, cpx<float>(&oa)[5], cpx<float>(&ob)[5]) {
             if (POT) {
-                potential_site<float, true>(oa, ob, PC, inv_sigma2, out_scale, status);
+                potential_site<float, true>(oa, ob, PC, 1.0f / 65536.0f, 0.5f / 256.0f, status);
             } else {
                 const float s = 1.0f / 256.0f;
 #pragma unroll
@@ -230,13 +243,11 @@ __device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float
                     ob[m] = s * ob[m];
                 }
             }
-            const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + lane;
+            const int64_t site = int64_t(y) * nx + x0 + lane;
 #pragma unroll
             for (int m = 0; m < 5; ++m)
                 out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
-        }
-    }
-    cp_async_wait<0>();
+        });
 }
 
 // The kernel.  POT = false applies the kinetic operator alone (out = K X), used to read out a

@@ -239,6 +239,41 @@ def test_observables(precision, ndim, nx, ny):
     assert abs(o["singlet_fraction"] - w["singlet_fraction"]) <= (1e-10 if precision == 64 else 1e-6)
 
 
+# A 2D FP32 state held pending K is read out in one pass (K applied in the warp strips, the
+# sums in the same pass; the +x pairs across strip edges through edge buffers; each row chunk
+# starts one row early for its -y pair).  Shapes: one strip whose edge pair wraps onto itself
+# (nx = 32), one-row chunks (ny = 8), ragged chunks, several strips.
+@pytest.mark.parametrize("nx,ny,variant", [(32, 8, 0), (96, 13, 1), (256, 67, 0), (512, 300, 1)])
+def test_observables_fused_readout(nx, ny, variant):
+    rng = np.random.default_rng(41 + nx + ny)
+    st = I.random_state(rng, nx, ny, scale=0.05).astype(np.float32)
+    ref_st = I.random_state(rng, nx, ny, scale=0.05).astype(np.float32)
+    ref_dev = torch.from_numpy(ref_st).cuda()
+    g = G_SETS[1]
+    lat = qlga.Lattice(2, nx, ny, precision=32, g=g, kinetic_variant=variant)
+    lat.load_state(st)
+    lat.step(7)                                          # held pending K
+    assert lat.step2d_kernel() == qlga.QLGA_STEP2D_FUSED
+    o = lat.observables(ref=ref_dev)
+    o_again = lat.observables(ref=ref_dev)
+    true = lat.get_state()                               # K X from the same strip arithmetic
+    lat.set_step2d_mode(qlga.QLGA_STEP2D_TWO_PASS)
+    o_two = lat.observables(ref=ref_dev)                 # materialised state, separate pass
+    lat.close()
+    cfg = oracle.make_cfg(2, nx, ny, *g, kinetic_variant=variant)
+    w = oracle.observables(np.ascontiguousarray(true, dtype=np.float64), cfg,
+                           ref=np.ascontiguousarray(ref_st, dtype=np.float64))
+    scale = w["norm_qubit"]
+    keys = ("norm_qubit", "norm_boson", "magnetisation", "energy", "singlet_re", "singlet_im",
+            "overlap_re", "overlap_im")
+    for k in keys:
+        assert o[k] == o_again[k], k                     # fixed summation order
+        assert abs(o[k] - w[k]) <= 1e-6 * scale, k       # FP32 terms of the same FP32 state
+        assert abs(o[k] - o_two[k]) <= 2e-6 * scale, k   # the two-pass K rounds differently
+    np.testing.assert_allclose(o["pop"], w["pop"], rtol=0, atol=1e-6 * scale)
+    assert abs(o["singlet_fraction"] - w["singlet_fraction"]) <= 1e-6
+
+
 # ------------------------------------------------------------------ the paper's workloads
 
 def test_config0_bright_soliton_full_run_fp64():

@@ -5,8 +5,10 @@ allocator or to a fixed memory plan (a cudaMalloc from the library could fail or
 pool), or they run time-critical loops that must not stall on cudaMalloc / cudaFree.  For them
 qlga_observables_noalloc() keeps its reduction scratch in a static device array.  This file is
 collected last; it calls that entry point through the C ABI, twice in a row on different states,
-and checks each result against qlga_observables() within the tolerance of the other observable
-tests (1e-12 of the norm).
+and checks each result against qlga_observables(): within 1e-12 of the norm for an FP64 state;
+within 1e-8 of each quantity's scale for an FP32 state, whose FP32 per-site terms the handle may
+form and sum in another order (a 2D state held pending K is read out in one fused pass; the two
+differ by ~3e-10) -- far below what a leak of the first call's scratch into the second would leave.
 """
 import ctypes
 
@@ -22,7 +24,6 @@ if not torch.cuda.is_available():
 from paper_1907_12834_gb300 import inputs as I  # noqa: E402
 from paper_1907_12834_gb300 import qlga  # noqa: E402
 
-TOL = 1e-12
 KEYS = ("norm_qubit", "norm_boson", "magnetisation", "energy", "singlet_re", "singlet_im",
         "singlet_fraction", "overlap_re", "overlap_im")
 
@@ -36,11 +37,13 @@ def call_noalloc(cfg, state_ptr, ref_ptr, stream):
     return status, qlga.obs_to_dict(out)
 
 
-def assert_same(got, want):
+def assert_same(got, want, precision):
+    tol = 1e-12 if precision == 64 else 1e-8
     scale = want["norm_qubit"]
     for k in KEYS:
-        assert abs(got[k] - want[k]) <= TOL * max(scale, 1.0), (k, got[k], want[k])
-    np.testing.assert_allclose(got["pop"], want["pop"], rtol=0, atol=TOL * scale)
+        ks = max(scale, 1.0) if precision == 64 else max(scale, abs(want[k]), 1.0)
+        assert abs(got[k] - want[k]) <= tol * ks, (k, got[k], want[k])
+    np.testing.assert_allclose(got["pop"], want["pop"], rtol=0, atol=tol * scale)
 
 
 @pytest.mark.parametrize("precision,ndim,nx,ny", [(32, 2, 300, 257), (64, 1, 5000, 1),
@@ -59,7 +62,7 @@ def test_noalloc_observables_match_twice_in_a_row(precision, ndim, nx, ny):
     want1 = lat.observables(ref=ref)
     status, got1 = call_noalloc(lat.cfg, s1.data_ptr(), ref.data_ptr(), stream)
     assert status == qlga.QLGA_OK, qlga.qlga_last_error()
-    assert_same(got1, want1)
+    assert_same(got1, want1, precision)
 
     # second call, on a later state and without a reference: nothing of the first call leaks in
     lat.step(3)
@@ -70,7 +73,7 @@ def test_noalloc_observables_match_twice_in_a_row(precision, ndim, nx, ny):
     status, got2 = call_noalloc(lat.cfg, s2.data_ptr(), 0, stream)
     free_after = torch.cuda.mem_get_info()[0]
     assert status == qlga.QLGA_OK, qlga.qlga_last_error()
-    assert_same(got2, want2)
+    assert_same(got2, want2, precision)
     assert got2["overlap_re"] == 0.0 and got2["overlap_im"] == 0.0
     assert free_after == free_before
     lat.close()

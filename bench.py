@@ -396,7 +396,8 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     lat.close()
     out["batched_fp32_1d"] = {"runs": int(len(bw.lengths)), "sites": total, "site_updates_per_s": total / sec,
                               "ms_per_step": sec * 1e3, "tile_width": info["tile_width"],
-                              "sites_per_thread": info["sites_per_thread"]}
+                              "sites_per_thread": info["sites_per_thread"],
+                              "steps_per_launch": info["steps_per_launch"]}
     out["single_run_fp64_1d"] = {"lattice": L, "site_updates_per_s": L / sec1, "ms_per_step": sec1 * 1e3}
     out["batched_fp32_over_single_run_fp64"] = (total / sec) / (L / sec1)
     # batched 2D (128 runs of 64..512 x 64..512 sites, FP32) against one FP64 run of the batch

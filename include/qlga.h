@@ -207,6 +207,17 @@ qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps);
 qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode);
 qlga_status qlga_get_step2d_kernel(qlga_handle* h, int32_t* kernel);
 
+/* Launch shape of a 1D lattice's steps (the tiled kernel the batches use, tiles computed from the
+ * block index): the first fused step times the candidates on the live state and keeps the
+ * fastest one-step shape and, in FP32 plain steps, the fastest two-step shape (temporal blocking,
+ * see the batches) when it beats it per step; qlga_step then takes fused steps two per launch.
+ * qlga_set_1d_shape forces a shape (the list and the (0, 0, 0) reset of qlga_batch_set_shape);
+ * qlga_get_1d_shape reports the one fused steps use (zeros before tuning).  Setting waits for the
+ * handle's stream and drops captured step graphs.  Errors: QLGA_ERR_UNSUPPORTED on a 2D lattice,
+ * or two steps per launch in FP64 or with interleave; QLGA_ERR_INVALID_ARG for another shape. */
+qlga_status qlga_set_1d_shape(qlga_handle* h, int32_t threads, int32_t sites_per_thread, int32_t steps);
+qlga_status qlga_get_1d_shape(qlga_handle* h, int32_t* threads, int32_t* sites_per_thread, int32_t* steps);
+
 /* Number of kernels this handle has launched since creation (a diagnostic for benchmarks). */
 qlga_status qlga_launch_count(const qlga_handle* h, int64_t* count);
 
@@ -270,13 +281,16 @@ qlga_status qlga_adjoint_step(qlga_handle* h, const void* x_device, void* cot_de
  * Batches: many independent periodic lattices of uneven size, 1D and 2D, each with its own
  * couplings, advanced together.  The state buffer of a batch is the concatenation of the runs'
  * states, each in the layout above (run r starts at element 20 * sum_{s<r} nx_s ny_s).  Steps are
- * the plain step.  1D runs go through a tiled kernel in one launch per step; the first
- * qlga_batch_step() times its candidate launch shapes (tiles of 32 / 64 / 128 / 256 sites,
- * 1 / 2 / 4 sites per thread) on the live state (writing only work space) and keeps the fastest.
- * 2D runs (FP32; nx a multiple of 32) go through the fused warp-strip kernel of the single 2D
- * lattice, its warps reading their run, strip and row range from a task table, in one more
- * launch per step.  On a non-default stream, pairs of steps are replayed from a CUDA graph
- * captured once.
+ * the plain step.  1D runs go through a tiled kernel (Sec. VII.B's step on each tile and its
+ * periodic halo); the first qlga_batch_step() times its candidate launch shapes on the live state
+ * (writing only work space) and keeps the fastest: tiles of 32 / 64 / 128 / 256 sites at 1 / 2 / 4
+ * sites per thread, one step per launch, and -- FP32 batches of 1D runs only -- two steps per
+ * launch on tiles of 120 / 248 sites (temporal blocking: the tile and an 8-site halo are read
+ * once, the first step's result stays in shared memory; each site's arithmetic is unchanged), if
+ * that is faster per step.  2D runs (FP32; nx a multiple of 32) go through the fused warp-strip
+ * kernel of the single 2D lattice, its warps reading their run, strip and row range from a task
+ * table, in one more launch per step.  On a non-default stream, runs of steps (two launches) are
+ * replayed from a CUDA graph captured once.
  * --------------------------------------------------------------------------------------- */
 typedef struct qlga_batch_config {
     int32_t precision;       /* 32 or 64 (64: 1D runs only) */
@@ -308,11 +322,22 @@ qlga_status qlga_batch_step(qlga_batch* b, int64_t n);
 /* Observables of every run: out is a host array of nruns qlga_obs (FP64 sums); waits. */
 qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out);
 
-/* Launch shape chosen by the tuner (0 before the first step): tile width in sites and sites per
- * thread (the CTA has tile_width / sites_per_thread threads); kernels launched, and the number of
+/* Launch shape of the 1D runs' steps (0 before the first step): tile width in sites, sites per
+ * thread and fused steps per launch (1, or 2 with temporal blocking; the CTA has
+ * (tile_width + 8 (steps - 1)) / sites_per_thread threads); kernels launched, and the number of
  * steps taken through graph replays.  Any pointer may be NULL. */
 qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int32_t* sites_per_thread,
-                            int64_t* launches, int64_t* graph_steps);
+                            int64_t* launches, int64_t* graph_steps, int32_t* steps_per_launch);
+
+/* Force the launch shape of the 1D runs instead of timing the candidates: (threads per CTA,
+ * sites per thread, steps per launch) is one of (32, 1, 1), (64, 1, 1), (128, 1, 1), (256, 1, 1),
+ * (64, 2, 1), (128, 2, 1), (64, 4, 1), (64, 4, 2), (128, 2, 2), (64, 2, 2), (256, 1, 2); with two
+ * steps per launch, single steps (an odd count) take the same threads and sites per thread.
+ * (0, 0, 0) returns to timing the candidates at the next step.  Results agree with every shape
+ * to rounding (the Taylor degree of U is a warp maximum).  Waits for the batch's stream and drops
+ * its captured graph.  Errors: QLGA_ERR_INVALID_ARG for another shape, QLGA_ERR_UNSUPPORTED for
+ * two steps per launch in an FP64 batch or one with 2D runs. */
+qlga_status qlga_batch_set_shape(qlga_batch* b, int32_t threads, int32_t sites_per_thread, int32_t steps);
 
 qlga_status qlga_batch_destroy(qlga_batch* b);
 

@@ -644,16 +644,27 @@ inline int obs2d_f32_launch(const float* in, const float* ref, int64_t nx, int64
 
 namespace qlga {
 
-constexpr int kBatchNumWidths = 4;
-constexpr int kBatchWidths[kBatchNumWidths] = {32, 64, 128, 256};  // tile widths (sites)
+constexpr int kBatchNumWidths = 6;
+constexpr int kBatchWidths[kBatchNumWidths] = {32, 64, 128, 256, 120, 248};  // tile widths (sites)
 
+// A launch shape: tile width (index into kBatchWidths) = threads x sites per thread - 8 (steps - 1),
+// steps = fused steps per launch (2: temporal blocking, FP32 only).
 struct BatchCand {
-    int tile, threads, spt;  // tile: index into kBatchWidths
+    int tile, threads, spt, steps;
 };
-constexpr int kBatchNumCands = 7;
-constexpr BatchCand kBatchCands[kBatchNumCands] = {{0, 32, 1}, {1, 64, 1}, {2, 128, 1}, {3, 256, 1},
-                                                   {2, 64, 2}, {3, 128, 2}, {3, 64, 4}};
+constexpr int kBatchNumCands = 11;
+constexpr BatchCand kBatchCands[kBatchNumCands] = {
+    {0, 32, 1, 1},  {1, 64, 1, 1},  {2, 128, 1, 1}, {3, 256, 1, 1}, {2, 64, 2, 1},  {3, 128, 2, 1},
+    {3, 64, 4, 1},  {5, 64, 4, 2},  {5, 128, 2, 2}, {4, 64, 2, 2},  {5, 256, 1, 2}};
 constexpr int kBatchDefaultCand = 1;  // before tuning: 64 threads, one site each
+
+// Candidate index of a shape (threads, sites per thread, steps), -1 if there is none.
+inline int batch_cand_of(int threads, int spt, int steps) {
+    for (int ci = 0; ci < kBatchNumCands; ++ci)
+        if (kBatchCands[ci].threads == threads && kBatchCands[ci].spt == spt && kBatchCands[ci].steps == steps)
+            return ci;
+    return -1;
+}
 
 struct TileArgs {
     cudaStream_t stream;
@@ -670,12 +681,12 @@ struct TileArgs {
     PotParams single_params;
 };
 
-template <class T, int V, bool POT, int W, int SPT>
+template <class T, int V, bool POT, int W, int SPT, int STEPS>
 void tile_launch_shape(const TileArgs& a) {
-    constexpr int TW = W * SPT;
-    const int nb = a.tiles ? a.ntiles : int((a.single_L + TW - 1) / TW);
+    constexpr int TOUT = W * SPT - 8 * (STEPS - 1);
+    const int nb = a.tiles ? a.ntiles : int((a.single_L + TOUT - 1) / TOUT);
     const PotConst<T> pc = a.tiles ? PotConst<T>() : PotConst<T>(a.single_params);
-    k_batch_step<T, V, POT, W, SPT><<<nb, W, 0, a.stream>>>(
+    k_batch_step<T, V, POT, W, SPT, STEPS><<<nb, W, 0, a.stream>>>(
         static_cast<const T*>(a.in), static_cast<T*>(a.out), a.tiles, a.runs,
         static_cast<const PotConst<T>*>(a.consts), a.status, int(a.single_L), pc);
 }
@@ -683,17 +694,33 @@ void tile_launch_shape(const TileArgs& a) {
 template <class T, int V, bool POT>
 void tile_launch_cand(const TileArgs& a, int ci) {
     switch (ci) {
-        case 0: tile_launch_shape<T, V, POT, 32, 1>(a); break;
-        case 1: tile_launch_shape<T, V, POT, 64, 1>(a); break;
-        case 2: tile_launch_shape<T, V, POT, 128, 1>(a); break;
-        case 3: tile_launch_shape<T, V, POT, 256, 1>(a); break;
-        case 4: tile_launch_shape<T, V, POT, 64, 2>(a); break;
-        case 5: tile_launch_shape<T, V, POT, 128, 2>(a); break;
-        default: tile_launch_shape<T, V, POT, 64, 4>(a); break;
+        case 0: tile_launch_shape<T, V, POT, 32, 1, 1>(a); return;
+        case 1: tile_launch_shape<T, V, POT, 64, 1, 1>(a); return;
+        case 2: tile_launch_shape<T, V, POT, 128, 1, 1>(a); return;
+        case 3: tile_launch_shape<T, V, POT, 256, 1, 1>(a); return;
+        case 4: tile_launch_shape<T, V, POT, 64, 2, 1>(a); return;
+        case 5: tile_launch_shape<T, V, POT, 128, 2, 1>(a); return;
+        case 6: tile_launch_shape<T, V, POT, 64, 4, 1>(a); return;
+        default: break;
+    }
+    if constexpr (sizeof(T) == 4 && POT) {  // two steps per launch: FP32 fused steps only
+        switch (ci) {
+            case 7: tile_launch_shape<T, V, POT, 64, 4, 2>(a); return;
+            case 8: tile_launch_shape<T, V, POT, 128, 2, 2>(a); return;
+            case 9: tile_launch_shape<T, V, POT, 64, 2, 2>(a); return;
+            case 10: tile_launch_shape<T, V, POT, 256, 1, 2>(a); return;
+            default: break;
+        }
     }
 }
 
-// Launch k_batch_step with shape ci (errors left in cudaGetLastError()).
+// Whether shape ci runs for this precision and kind of launch (two-step shapes: FP32 fused steps).
+inline bool tile_cand_ok(int precision, bool pot, int ci) {
+    return ci >= 0 && ci < kBatchNumCands && (kBatchCands[ci].steps == 1 || (precision == 32 && pot));
+}
+
+// Launch k_batch_step with shape ci (errors left in cudaGetLastError()); ci must pass
+// tile_cand_ok.
 inline void tile_step_launch(const TileArgs& a, int ci) {
     if (a.precision == 32) {
         if (a.variant == 0) { if (a.pot) tile_launch_cand<float, 0, true>(a, ci); else tile_launch_cand<float, 0, false>(a, ci); }
@@ -722,6 +749,7 @@ struct qlga_handle {
     int64_t step;
     int64_t launches;  // kernels launched by this handle
     int tile_cand;  // 1D: launch shape of the tiled step (index into kBatchCands), -1 untuned
+    int tile_cand2;  // 1D: two-step shape when it beats tile_cand per step, else -1
     int step2d_mode;  // QLGA_STEP2D_AUTO / _FUSED / _TWO_PASS
     // CUDA graphs of graph_steps fused steps starting (and ending) on buffer 0 or 1
     int graph_steps;
@@ -864,43 +892,112 @@ struct EventPair {
     }
 };
 
-// 1D: the tiled step kernel (shared with the batches) on the whole lattice, in -> out.  The first
-// fused step times the launch shapes on the live state, writing only `out`, and keeps the
-// fastest.
-qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot) {
+// Times the launch shapes on the live state: launch(ci, stream) issues one launch of shape ci on
+// `stream` (writing only work space or the step's output).  The cost compared is the time per
+// step.  Direct: a warm-up launch, then two timed ones on `stream`.  Graphed (where the steps will
+// be replayed from graphs, which hide the host's launch gaps): 4 steps of the shape captured into
+// a graph on a capture stream, one warm-up replay, then two timed replays.  best1 is the fastest
+// one-step shape; best2 the fastest two-step shape if `two_step` allows them and it beats best1
+// per step, else -1.
+template <class Launch>
+cudaError_t tune_shapes(cudaStream_t stream, bool two_step, bool graphed, Launch&& launch, int* best1, int* best2) {
+    EventPair ev;
+    cudaError_t e = ev.create();
+    cudaStream_t cs = nullptr;
+    if (e == cudaSuccess && graphed) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    float t1 = 1e30f, t2 = 1e30f;
+    *best1 = kBatchDefaultCand;
+    *best2 = -1;
+    for (int ci = 0; ci < kBatchNumCands && e == cudaSuccess; ++ci) {
+        const int steps = kBatchCands[ci].steps;
+        if (steps == 2 && !two_step) continue;
+        float ms = 0.f;
+        if (graphed) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t x = nullptr;
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                for (int k = 0; k < 4 / steps; ++k) launch(ci, cs);
+                e = cudaStreamEndCapture(cs, &g);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) e = cudaGraphLaunch(x, stream);  // warm
+            if (e == cudaSuccess) e = cudaEventRecord(ev.e0, stream);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaGraphLaunch(x, stream);
+            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+            if (x) cudaGraphExecDestroy(x);
+            ms /= 8.f;  // two replays of 4 steps
+        } else {
+            launch(ci, stream);  // warm
+            e = cudaEventRecord(ev.e0, stream);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) launch(ci, stream);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+            ms /= float(2 * steps);
+        }
+        if (e != cudaSuccess) break;
+        if (steps == 1 && ms < t1) {
+            t1 = ms;
+            *best1 = ci;
+        } else if (steps == 2 && ms < t2) {
+            t2 = ms;
+            *best2 = ci;
+        }
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (*best2 >= 0 && !(t2 < t1)) *best2 = -1;
+    return e;
+}
+
+// Number of kernel launches tune_shapes issues.
+inline int tune_launches(bool two_step, bool graphed) {
+    int n = 0;
+    for (int ci = 0; ci < kBatchNumCands; ++ci) {
+        const int steps = kBatchCands[ci].steps;
+        if (steps == 2 && !two_step) continue;
+        n += graphed ? 3 * (4 / steps) : 3;
+    }
+    return n;
+}
+
+// 1D: the tiled step kernel (shared with the batches) on the whole lattice, in -> out; `steps`
+// fused steps (2: the two-step shape, which the handle has only in FP32 and when it is faster).
+// The first fused step times the launch shapes on the live state, writing only `out`, and keeps
+// the fastest one-step and two-step shapes.
+qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot, int steps = 1) {
     TileArgs a{h->stream, h->cfg.precision, h->cfg.kinetic_variant, pot, in, out, nullptr, 0, nullptr,
                nullptr, h->status, h->cfg.nx, pot_params(h->cfg, 1.0)};
     if (pot && h->tile_cand < 0) {
-        EventPair ev;
-        cudaError_t e = ev.create();
-        float best = 1e30f;
-        int besti = kBatchDefaultCand;
-        for (int ci = 0; ci < kBatchNumCands && e == cudaSuccess; ++ci) {
-            tile_step_launch(a, ci);  // warm
-            e = cudaEventRecord(ev.e0, h->stream);
-            for (int k = 0; k < 2 && e == cudaSuccess; ++k) tile_step_launch(a, ci);
-            if (e == cudaSuccess) e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, h->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
-            if (e == cudaSuccess && ms < best) {
-                best = ms;
-                besti = ci;
-            }
-        }
+        const bool two = h->cfg.precision == 32 && !h->cfg.interleave;
+        const bool graphed = h->graph_steps > 0;
+        cudaError_t e = tune_shapes(h->stream, two, graphed,
+                                    [&](int ci, cudaStream_t st) {
+                                        TileArgs b = a;
+                                        b.stream = st;
+                                        tile_step_launch(b, ci);
+                                    },
+                                    &h->tile_cand, &h->tile_cand2);
         if (e != cudaSuccess) return cuda_fail(e, "1D step tuning");
-        h->launches += 3 * kBatchNumCands;
-        h->tile_cand = besti;
+        h->launches += tune_launches(two, graphed);
     }
-    tile_step_launch(a, h->tile_cand >= 0 ? h->tile_cand : kBatchDefaultCand);
+    const int ci = steps == 2 ? h->tile_cand2 : (h->tile_cand >= 0 ? h->tile_cand : kBatchDefaultCand);
+    if (!tile_cand_ok(h->cfg.precision, pot, ci)) return fail(QLGA_ERR_INVALID_ARG, "no launch shape for this 1D step%s");
+    tile_step_launch(a, ci);
     QLGA_CUDA(cudaGetLastError(), "k_batch_step launch (1D)");
     h->launches += 1;
     return QLGA_OK;
 }
 
-// Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
-// x pass.  With pot, U follows the last axis (the fused step).
+// Whether the next fused steps of this handle can go two per launch (1D FP32, tuned or forced).
+bool two_step_1d(const qlga_handle* h) {
+    return h->cfg.ndim == 1 && !h->cfg.interleave && h->pending_k && h->tile_cand2 >= 0;
+}
+
 // The 2D kernel form of this handle's steps (see qlga_set_step2d_mode).
 bool step2d_uses_fused(const qlga_handle* h) {
     if (h->cfg.ndim != 2 || !step2d_f32_supported(h->cfg.nx, h->cfg.ny)) return false;
@@ -909,6 +1006,8 @@ bool step2d_uses_fused(const qlga_handle* h) {
     return h->cfg.precision == 32 || step2d_f64_fused_preferred(h->cfg.nx, h->cfg.ny);
 }
 
+// Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
+// x pass.  With pot, U follows the last axis (the fused step).
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
     if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
     if (step2d_uses_fused(h)) {
@@ -1006,7 +1105,15 @@ qlga_status graph_steps_launch(qlga_handle* h) {
         if (e == cudaSuccess) {
             h->stream = cs;
             int c = h->cur;
-            for (int k = 0; k < h->graph_steps && s == QLGA_OK; ++k) {
+            // two fused steps per launch where the handle has them (1D FP32), with an even number
+            // of launches so that the graph ends on the buffer it starts from
+            const int gs = h->graph_steps;
+            const int twos = two_step_1d(h) ? (gs % 4 == 0 ? gs / 2 : (gs - 2) / 2) : 0;
+            for (int k = 0; k < twos && s == QLGA_OK; ++k) {
+                s = tile_1d(h, h->X[c], h->X[1 - c], true, 2);
+                c ^= 1;
+            }
+            for (int k = 2 * twos; k < gs && s == QLGA_OK; ++k) {
                 s = kinetic_into(h, h->X[c], h->X[1 - c], h->tmp, true);
                 c ^= 1;
             }
@@ -1166,6 +1273,7 @@ static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* str
     h->graph_launches = 0;
     h->graph[0] = h->graph[1] = nullptr;
     h->tile_cand = -1;
+    h->tile_cand2 = -1;
     h->step2d_mode = QLGA_STEP2D_AUTO;
     QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
     QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
@@ -1291,6 +1399,14 @@ qlga_status qlga_step(qlga_handle* h, int64_t n) {
             if (s != QLGA_OK) return s;
             h->step += h->graph_steps;
             i += h->graph_steps - 1;
+            continue;
+        }
+        if (two_step_1d(h) && n - i >= 2) {  // two fused steps in one launch
+            s = tile_1d(h, h->X[h->cur], h->X[1 - h->cur], true, 2);
+            if (s != QLGA_OK) return s;
+            h->cur ^= 1;
+            h->step += 2;
+            ++i;
             continue;
         }
         if (h->cfg.interleave) {
@@ -1455,6 +1571,34 @@ qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode) {
 qlga_status qlga_get_step2d_kernel(qlga_handle* h, int32_t* kernel) {
     if (!h || !kernel) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
     *kernel = h->cfg.ndim != 2 ? 0 : (step2d_uses_fused(h) ? QLGA_STEP2D_FUSED : QLGA_STEP2D_TWO_PASS);
+    return QLGA_OK;
+}
+
+qlga_status qlga_set_1d_shape(qlga_handle* h, int32_t threads, int32_t sites_per_thread, int32_t steps) {
+    if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->cfg.ndim != 1) return fail(QLGA_ERR_UNSUPPORTED, "launch shapes are for 1D lattices%s");
+    int c1 = -1, c2 = -1;
+    if (threads != 0 || sites_per_thread != 0 || steps != 0) {
+        const int ci = batch_cand_of(threads, sites_per_thread, steps);
+        if (ci < 0) return fail(QLGA_ERR_INVALID_ARG, "not one of the launch shapes%s");
+        if (steps == 2 && (h->cfg.precision != 32 || h->cfg.interleave))
+            return fail(QLGA_ERR_UNSUPPORTED, "two steps per launch need FP32 plain steps%s");
+        c1 = steps == 2 ? batch_cand_of(threads, sites_per_thread, 1) : ci;
+        c2 = steps == 2 ? ci : -1;
+    }
+    cudaStreamSynchronize(h->stream);
+    graphs_release(h);
+    h->tile_cand = c1;
+    h->tile_cand2 = c2;
+    return QLGA_OK;
+}
+
+qlga_status qlga_get_1d_shape(qlga_handle* h, int32_t* threads, int32_t* sites_per_thread, int32_t* steps) {
+    if (!h || !threads || !sites_per_thread || !steps) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    const int ci = h->tile_cand2 >= 0 ? h->tile_cand2 : h->tile_cand;
+    *threads = ci >= 0 ? kBatchCands[ci].threads : 0;
+    *sites_per_thread = ci >= 0 ? kBatchCands[ci].spt : 0;
+    *steps = ci >= 0 ? kBatchCands[ci].steps : 0;
     return QLGA_OK;
 }
 
@@ -1736,11 +1880,13 @@ struct qlga_batch {
     WarpTask* tasks;          // warp tasks of the 2D runs
     int ntasks;
     int wsel;                 // index into kBatchCands, -1 before tuning
+    int wsel2;                // two-step shape when it beats wsel per step (FP32, 1D runs only), else -1
     int cur;
     bool pending_k;
     int64_t step, launches, graph_steps;
     cudaGraphExec_t graph;
-    int graph_cur;            // X index the captured pair of steps starts from, -1 if none
+    int graph_cur;            // X index the captured steps start from, -1 if none
+    int graph_nsteps, graph_nlaunches;  // steps and kernel launches per graph replay
 };
 
 namespace {
@@ -1851,41 +1997,33 @@ qlga_status batch_potential(qlga_batch* b, void* X) {
 qlga_status batch_tune(qlga_batch* b) {
     if (b->ntiles[0] == 0) {  // no 1D runs: nothing to tune
         b->wsel = kBatchDefaultCand;
+        b->wsel2 = -1;
         return QLGA_OK;
     }
-    EventPair ev;
-    QLGA_CUDA(ev.create(), "tune event");
-    float best = 1e30f;
-    int besti = kBatchDefaultCand;
-    for (int wi = 0; wi < kBatchNumCands; ++wi) {
-        qlga_status s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);  // warm
-        if (s != QLGA_OK) return s;
-        QLGA_CUDA(cudaEventRecord(ev.e0, b->stream), "tune record");
-        for (int k = 0; k < 2; ++k) {
-            s = batch_launch(b, b->X[b->cur], b->tmp, true, wi);
-            if (s != QLGA_OK) return s;
-        }
-        QLGA_CUDA(cudaEventRecord(ev.e1, b->stream), "tune record");
-        QLGA_CUDA(cudaEventSynchronize(ev.e1), "tune sync");
-        float ms = 0.f;
-        QLGA_CUDA(cudaEventElapsedTime(&ms, ev.e0, ev.e1), "tune elapsed");
-        if (ms < best) {
-            best = ms;
-            besti = wi;
-        }
-    }
-    b->wsel = besti;
+    const bool two = b->precision == 32 && b->ntasks == 0;
+    cudaError_t e = tune_shapes(b->stream, two, b->use_graph,
+                                [&](int ci, cudaStream_t st) {
+                                    cudaStream_t saved = b->stream;
+                                    b->stream = st;
+                                    batch_launch(b, b->X[b->cur], b->tmp, true, ci);
+                                    b->stream = saved;
+                                },
+                                &b->wsel, &b->wsel2);
+    if (e != cudaSuccess) return cuda_fail(e, "batch step tuning");
     return QLGA_OK;
 }
 
-// Capture two fused steps starting from X[cur] (cur -> 1-cur -> cur) into a graph.
+// Capture fused steps starting from X[cur] into a graph: two launches, cur -> 1-cur -> cur, of
+// the two-step shape (4 steps) or of the one-step shape (2 steps).
 qlga_status batch_build_graph(qlga_batch* b) {
     cudaGraph_t g;
     QLGA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "graph capture begin");
     const int c = b->cur;
+    const int ci = b->wsel2 >= 0 ? b->wsel2 : b->wsel;
     const int64_t l0 = b->launches;
-    qlga_status s1 = batch_launch(b, b->X[c], b->X[1 - c], true, b->wsel);
-    qlga_status s2 = s1 == QLGA_OK ? batch_launch(b, b->X[1 - c], b->X[c], true, b->wsel) : s1;
+    qlga_status s1 = batch_launch(b, b->X[c], b->X[1 - c], true, ci);
+    qlga_status s2 = s1 == QLGA_OK ? batch_launch(b, b->X[1 - c], b->X[c], true, ci) : s1;
+    b->graph_nlaunches = int(b->launches - l0);
     b->launches = l0;  // counted when replayed
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (s2 != QLGA_OK) return s2;
@@ -1894,6 +2032,7 @@ qlga_status batch_build_graph(qlga_batch* b) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
     b->graph_cur = c;
+    b->graph_nsteps = 2 * kBatchCands[ci].steps;
     return QLGA_OK;
 }
 
@@ -1934,6 +2073,9 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
     b->total_sites = total;
     b->stream = static_cast<cudaStream_t>(stream);
     b->wsel = -1;
+    b->wsel2 = -1;
+    b->graph_nsteps = 0;
+    b->graph_nlaunches = 0;
     b->graph_cur = -1;
     const size_t sb = batch_state_bytes_of(cfg->precision, total);
     std::vector<BatchRun> runs(cfg->nruns);
@@ -2077,29 +2219,33 @@ qlga_status qlga_batch_step(qlga_batch* b, int64_t n) {
             s = batch_potential(b, b->X[b->cur]);  // X = U psi, true state K X
             if (s != QLGA_OK) return s;
             b->pending_k = true;
-        } else {
-            if (b->wsel < 0) {
-                s = batch_tune(b);
-                if (s != QLGA_OK) return s;
-            }
-            if (b->use_graph && n >= 2 && b->graph_cur < 0) {
-                s = batch_build_graph(b);
-                if (s != QLGA_OK) return s;
-            }
-            if (b->use_graph && n >= 2 && b->graph_cur == b->cur) {
-                QLGA_CUDA(cudaGraphLaunch(b->graph, b->stream), "graph launch");
-                b->launches += 2;
-                b->graph_steps += 2;
-                b->step += 2;
-                n -= 2;
-                continue;
-            }
-            s = batch_launch(b, b->X[b->cur], b->X[1 - b->cur], true, b->wsel);
-            if (s != QLGA_OK) return s;
-            b->cur ^= 1;
+            b->step += 1;
+            n -= 1;
+            continue;
         }
-        b->step += 1;
-        n -= 1;
+        if (b->wsel < 0) {
+            s = batch_tune(b);
+            if (s != QLGA_OK) return s;
+        }
+        const int64_t per_replay = b->wsel2 >= 0 ? 4 : 2;
+        if (b->use_graph && n >= per_replay && b->graph_cur < 0) {
+            s = batch_build_graph(b);
+            if (s != QLGA_OK) return s;
+        }
+        if (b->use_graph && n >= b->graph_nsteps && b->graph_cur == b->cur) {
+            QLGA_CUDA(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+            b->launches += b->graph_nlaunches;
+            b->graph_steps += b->graph_nsteps;
+            b->step += b->graph_nsteps;
+            n -= b->graph_nsteps;
+            continue;
+        }
+        const int steps = (b->wsel2 >= 0 && n >= 2) ? 2 : 1;
+        s = batch_launch(b, b->X[b->cur], b->X[1 - b->cur], true, steps == 2 ? b->wsel2 : b->wsel);
+        if (s != QLGA_OK) return s;
+        b->cur ^= 1;
+        b->step += steps;
+        n -= steps;
     }
     return QLGA_OK;
 }
@@ -2147,12 +2293,35 @@ qlga_status qlga_batch_observables(qlga_batch* b, qlga_obs* out) {
 }
 
 qlga_status qlga_batch_info(const qlga_batch* b, int32_t* tile_width, int32_t* sites_per_thread, int64_t* launches,
-                            int64_t* graph_steps) {
+                            int64_t* graph_steps, int32_t* steps_per_launch) {
     if (!b) return fail(QLGA_ERR_INVALID_ARG, "batch is NULL%s");
-    if (tile_width) *tile_width = b->wsel >= 0 ? kBatchWidths[kBatchCands[b->wsel].tile] : 0;
-    if (sites_per_thread) *sites_per_thread = b->wsel >= 0 ? kBatchCands[b->wsel].spt : 0;
+    const int ci = b->wsel2 >= 0 ? b->wsel2 : b->wsel;
+    if (tile_width) *tile_width = ci >= 0 ? kBatchWidths[kBatchCands[ci].tile] : 0;
+    if (sites_per_thread) *sites_per_thread = ci >= 0 ? kBatchCands[ci].spt : 0;
+    if (steps_per_launch) *steps_per_launch = ci >= 0 ? kBatchCands[ci].steps : 0;
     if (launches) *launches = b->launches;
     if (graph_steps) *graph_steps = b->graph_steps;
+    return QLGA_OK;
+}
+
+qlga_status qlga_batch_set_shape(qlga_batch* b, int32_t threads, int32_t sites_per_thread, int32_t steps) {
+    if (!b) return fail(QLGA_ERR_INVALID_ARG, "batch is NULL%s");
+    int w1 = -1, w2 = -1;
+    if (threads != 0 || sites_per_thread != 0 || steps != 0) {
+        const int ci = batch_cand_of(threads, sites_per_thread, steps);
+        if (ci < 0) return fail(QLGA_ERR_INVALID_ARG, "not one of the launch shapes%s");
+        if (steps == 2 && (b->precision != 32 || b->ntasks > 0))
+            return fail(QLGA_ERR_UNSUPPORTED, "two steps per launch need an FP32 batch of 1D runs%s");
+        w1 = steps == 2 ? batch_cand_of(threads, sites_per_thread, 1) : ci;
+        w2 = steps == 2 ? ci : -1;
+    }
+    cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_cur = -1;
+    b->graph_nsteps = 0;
+    b->wsel = w1;
+    b->wsel2 = w2;
     return QLGA_OK;
 }
 

@@ -61,35 +61,67 @@ __device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T
     }
 }
 
-// One fused step (POT) or the kinetic operator alone, for the tiles of a batch.  A CTA of W
-// threads takes a tile of W * SPT consecutive sites of one run (thread t owns sites t, t + W, ...):
-// the tile and its 4-site periodic halo on each side are staged in shared memory with 16-byte
-// cp.async copies, all in flight at once, then each thread computes its SPT sites.
+// The kinetic operator (nine-point stencil of the axis, Sec. VII.B) at staged column p of src,
+// a shared-memory array of 5 planes of `stride` pairs: the site whose neighbourhood is columns
+// p .. p + 8.  Returns (a, b) 16 times the true value (the collides' factors dropped).
+template <class T, int VARIANT>
+__device__ __forceinline__ void batch_kinetic_at(const Pair4<T>* src, int stride, int p, cpx<T> oa[5],
+                                                 cpx<T> ob[5]) {
+    constexpr KinStencil S = kStencil[VARIANT];
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
+#pragma unroll
+        for (int kk = 0; kk < 9; ++kk) {
+            const Pair4<T> q = src[m * stride + p + kk];
+            const T caa = T(S.g[0][0][kk]), cab = T(S.g[0][1][kk]);
+            const T cba = T(S.g[1][0][kk]), cbb = T(S.g[1][1][kk]);
+            xa.re = fma(caa, q.v[0], fma(cab, q.v[2], xa.re));
+            xa.im = fma(caa, q.v[1], fma(cab, q.v[3], xa.im));
+            xbt.re = fma(cba, q.v[0], fma(cbb, q.v[2], xbt.re));
+            xbt.im = fma(cba, q.v[1], fma(cbb, q.v[3], xbt.im));
+        }
+        oa[m] = xa;                 // x16, unnormalised
+        ob[m] = {xbt.im, -xbt.re};  // b = -i bt
+    }
+}
+
+// One fused step (POT) or the kinetic operator alone, for the tiles of a batch; with STEPS = 2,
+// two fused steps.  A CTA of W threads computes W * SPT consecutive sites of one run per pass
+// (thread t owns sites t, t + W, ...).  The tile and its periodic halo of 4 * STEPS sites on
+// each side are staged in shared memory with 16-byte cp.async copies, all in flight at once.
+// STEPS = 2 (temporal blocking): the first step covers the tile and 4 halo sites per side, into
+// a second shared buffer; the second step reads that buffer.  The tile is then W * SPT - 8
+// sites wide, so both passes fill the threads; the state is read and written once per two
+// steps, each site's arithmetic unchanged.
 // tiles == nullptr: one 1D lattice of single_L sites with constants single_pc; tile b starts at
-// site b * W * SPT, and no table is read.
-template <class T, int VARIANT, bool POT, int W, int SPT>
+// site b * (tile width), and no table is read.
+template <class T, int VARIANT, bool POT, int W, int SPT, int STEPS = 1>
 __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* __restrict__ out,
                                                    const BatchTile* __restrict__ tiles,
                                                    const BatchRun* __restrict__ runs,
                                                    const PotConst<T>* __restrict__ consts,
                                                    unsigned* status, int single_L,
                                                    PotConst<T> single_pc) {
-    constexpr int TW = W * SPT;
+    static_assert(STEPS == 1 || (STEPS == 2 && POT), "two steps per launch are fused steps");
+    constexpr int TW = W * SPT;                  // sites per pass
+    constexpr int TOUT = TW - 8 * (STEPS - 1);   // output sites of a tile
+    constexpr int H = 4 * STEPS;                 // staged halo per side: TOUT + 2 H = TW + 8
     __shared__ __align__(16) Pair4<T> sm[5][TW + 8];  // 16-byte aligned for cp.async
-    constexpr KinStencil S = kStencil[VARIANT];
+    __shared__ __align__(16) Pair4<T> mid[5][STEPS == 2 ? TW : 1];
     const bool single = tiles == nullptr;
-    const BatchTile tile = single ? BatchTile{0, int(blockIdx.x) * TW} : tiles[blockIdx.x];
+    const BatchTile tile = single ? BatchTile{0, int(blockIdx.x) * TOUT} : tiles[blockIdx.x];
     const BatchRun run = single ? BatchRun{0, single_L, 1} : runs[tile.run];
     const int L = run.L;
     const int t = threadIdx.x;
-    // staged column c holds site start - 4 + c of the run (periodic)
+    // staged column c holds site start - H + c of the run (periodic)
     auto wrap = [&](int j) {
         if (L >= TW + 8) return j < 0 ? j + L : (j >= L ? j - L : j);  // at most one wrap
         j %= L;
         return j < 0 ? j + L : j;
     };
     auto stage = [&](int c) {
-        const int j = wrap(tile.start - 4 + c);
+        const int j = wrap(tile.start - H + c);
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             const T* src = in + 4 * (run.base + int64_t(m) * L + j);
@@ -105,27 +137,29 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
     cp_async_wait<0>();
     __syncthreads();
     const PotConst<T> C = single ? single_pc : consts[tile.run];
+    if constexpr (STEPS == 2) {
+        // first step on columns 0 .. TW - 1 of mid: sites start - 4 .. start + TOUT + 3
+#pragma unroll 1
+        for (int k = 0; k < SPT; ++k) {
+            const int p = t + k * W;
+            cpx<T> oa[5], ob[5];
+            batch_kinetic_at<T, VARIANT>(&sm[0][0], TW + 8, p, oa, ob);
+            potential_site<T, sizeof(T) == 4>(oa, ob, C, T(1.0 / 256.0), T(0.5 / 16.0), status);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) mid[m][p] = Pair4<T>{{oa[m].re, oa[m].im, -ob[m].im, ob[m].re}};
+        }
+        __syncthreads();
+    }
+    const Pair4<T>* src = STEPS == 2 ? &mid[0][0] : &sm[0][0];
+    const int stride = STEPS == 2 ? TW : TW + 8;
 #pragma unroll 1
     for (int k = 0; k < SPT; ++k) {
         const int tt = t + k * W;
+        // positions past the tile's output (STEPS = 2: the last 8) redo a valid site and store nothing
+        const int p = tt < TOUT ? tt : TOUT - 1;
         const int j = tile.start + tt;
         cpx<T> oa[5], ob[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
-#pragma unroll
-            for (int kk = 0; kk < 9; ++kk) {
-                const Pair4<T> p = sm[m][tt + kk];
-                const T caa = T(S.g[0][0][kk]), cab = T(S.g[0][1][kk]);
-                const T cba = T(S.g[1][0][kk]), cbb = T(S.g[1][1][kk]);
-                xa.re = fma(caa, p.v[0], fma(cab, p.v[2], xa.re));
-                xa.im = fma(caa, p.v[1], fma(cab, p.v[3], xa.im));
-                xbt.re = fma(cba, p.v[0], fma(cbb, p.v[2], xbt.re));
-                xbt.im = fma(cba, p.v[1], fma(cbb, p.v[3], xbt.im));
-            }
-            oa[m] = xa;                  // x16, unnormalised
-            ob[m] = {xbt.im, -xbt.re};   // b = -i bt
-        }
+        batch_kinetic_at<T, VARIANT>(src, stride, p, oa, ob);
         if (POT) {
             // all lanes take part (the Taylor degree is a warp maximum); lanes past the run's end
             // work on a copy of a valid site and store nothing
@@ -137,7 +171,7 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
                 ob[m] = T(1.0 / 16.0) * ob[m];
             }
         }
-        if (j < L) {
+        if (tt < TOUT && j < L) {
 #pragma unroll
             for (int m = 0; m < 5; ++m)
                 store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);

@@ -90,7 +90,12 @@ _SIGNATURES = {
     "qlga_batch_step": [_H, ctypes.c_int64],
     "qlga_batch_observables": [_H, ctypes.POINTER(QlgaObs)],
     "qlga_batch_info": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int32)],
+    "qlga_batch_set_shape": [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+    "qlga_set_1d_shape": [_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+    "qlga_get_1d_shape": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32)],
     "qlga_batch_destroy": [_H],
     "qlga_destroy": [_H],
     "qlga_adjoint_workspace_bytes": [_CFG, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)],
@@ -449,6 +454,18 @@ class Lattice:
         """The 2D kernel form the next step uses (QLGA_STEP2D_FUSED / _TWO_PASS; 0 in 1D)."""
         return qlga_get_step2d_kernel(self.handle)
 
+    def set_1d_shape(self, threads=0, sites_per_thread=0, steps=0):
+        """Force the 1D launch shape (see qlga_set_1d_shape); zeros: time the candidates."""
+        _check(load_library().qlga_set_1d_shape(_H(self.handle), int(threads), int(sites_per_thread),
+                                                int(steps)), "qlga_set_1d_shape")
+
+    def shape_1d(self):
+        """(threads, sites per thread, steps per launch) of the fused 1D steps; zeros before tuning."""
+        t, spt, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load_library().qlga_get_1d_shape(_H(self.handle), ctypes.byref(t), ctypes.byref(spt),
+                                                ctypes.byref(st)), "qlga_get_1d_shape")
+        return t.value, spt.value, st.value
+
     def set_graph_steps(self, steps):
         """Steps per CUDA graph replay (even; 0 turns graphs off)."""
         qlga_set_graph_steps(self.handle, steps)
@@ -670,11 +687,17 @@ class Batch:
         return [obs_to_dict(o) for o in arr]
 
     def info(self):
-        w, spt, l, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        w, spt, l, g, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         _check(load_library().qlga_batch_info(_H(self.handle), ctypes.byref(w), ctypes.byref(spt),
-                                              ctypes.byref(l), ctypes.byref(g)), "qlga_batch_info")
+                                              ctypes.byref(l), ctypes.byref(g), ctypes.byref(st)),
+               "qlga_batch_info")
         return {"tile_width": w.value, "sites_per_thread": spt.value, "launches": l.value,
-                "graph_steps": g.value}
+                "graph_steps": g.value, "steps_per_launch": st.value}
+
+    def set_shape(self, threads=0, sites_per_thread=0, steps=0):
+        """Force the 1D runs' launch shape (see qlga_batch_set_shape); zeros: time the candidates."""
+        _check(load_library().qlga_batch_set_shape(_H(self.handle), int(threads), int(sites_per_thread),
+                                                   int(steps)), "qlga_batch_set_shape")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -60,8 +60,73 @@ def test_ragged_batch_matches_oracle_per_run(precision, use_graph, variant):
     tol = 1e-11 if precision == 64 else 2e-5
     for gr, rr in zip(got, ref):
         assert rel_l2(gr, rr) <= tol
-    assert info["tile_width"] in (32, 64, 128, 256) and info["sites_per_thread"] in (1, 2, 4)
+    assert info["tile_width"] in (32, 64, 128, 256, 120, 248) and info["sites_per_thread"] in (1, 2, 4)
+    assert info["steps_per_launch"] in ((1, 2) if precision == 32 else (1,))
     assert (info["graph_steps"] > 0) == use_graph
+
+
+# every launch shape of the tiled kernel, forced: one step per launch, and two (temporal blocking:
+# the tile plus an 8-site halo staged once; FP32); 13 steps = replays plus a single step; runs
+# shorter than a tile and its halo wrap several times
+SHAPES_1 = [(32, 1), (64, 1), (128, 1), (256, 1), (64, 2), (128, 2), (64, 4)]
+SHAPES_2 = [(64, 4), (128, 2), (64, 2), (256, 1)]
+
+
+@pytest.mark.parametrize("shape", [s + (1,) for s in SHAPES_1] + [s + (2,) for s in SHAPES_2])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_forced_shapes_match_oracle_per_run(shape, use_graph):
+    rng = np.random.default_rng(83)
+    couplings = np.column_stack([np.ones(len(LENGTHS)), rng.uniform(-1, 1, len(LENGTHS)),
+                                 rng.uniform(-1, 1, len(LENGTHS))])
+    state = np.concatenate([I.random_state(rng, L, scale=0.05).ravel() for L in LENGTHS]).astype(np.float32)
+    b = qlga.Batch(LENGTHS, couplings, precision=32, use_graph=use_graph)
+    b.set_shape(*shape)
+    b.load_state(state)
+    n = 13
+    b.step(n)
+    got = split(b.get_state(), LENGTHS)
+    info = b.info()
+    b.close()
+    ref = oracle_runs(state, LENGTHS, couplings, n)
+    for gr, rr, L in zip(got, ref, LENGTHS):
+        assert rel_l2(gr, rr) <= 2e-5, L
+    assert info["steps_per_launch"] == shape[2]
+    assert info["sites_per_thread"] == shape[1]
+    assert info["tile_width"] == shape[0] * shape[1] - 8 * (shape[2] - 1)
+
+
+@pytest.mark.parametrize("shape", [s + (1,) for s in SHAPES_1])
+def test_forced_shapes_fp64(shape):
+    rng = np.random.default_rng(89)
+    couplings = np.column_stack([np.ones(len(LENGTHS)), rng.uniform(-1, 1, len(LENGTHS)),
+                                 rng.uniform(-1, 1, len(LENGTHS))])
+    state = np.concatenate([I.random_state(rng, L, scale=0.05).ravel() for L in LENGTHS])
+    b = qlga.Batch(LENGTHS, couplings, precision=64)
+    b.set_shape(*shape)
+    b.load_state(state)
+    b.step(9)
+    got = split(b.get_state(), LENGTHS)
+    b.close()
+    for gr, rr in zip(got, oracle_runs(state, LENGTHS, couplings, 9)):
+        assert rel_l2(gr, rr) <= 1e-11
+
+
+def test_shape_errors():
+    g = [[1.0, 0.1, 0.2]] * 2
+    b = qlga.Batch([64, 100], g, precision=64)
+    for args, status in (((64, 4, 2), qlga.QLGA_ERR_UNSUPPORTED), ((63, 1, 1), qlga.QLGA_ERR_INVALID_ARG),
+                         ((64, 4, 3), qlga.QLGA_ERR_INVALID_ARG)):
+        with pytest.raises(qlga.QlgaError) as e:
+            b.set_shape(*args)
+        assert e.value.status == status
+    b.close()
+    b = qlga.Batch([64, 100], g, precision=32, heights=[16, 1])       # a 2D run: one step per launch
+    with pytest.raises(qlga.QlgaError) as e:
+        b.set_shape(64, 4, 2)
+    assert e.value.status == qlga.QLGA_ERR_UNSUPPORTED
+    b.set_shape(64, 4, 1)
+    b.set_shape()
+    b.close()
 
 
 def test_batch_observables_per_run():

@@ -210,6 +210,48 @@ def test_step_counts_and_pending_representation():
     assert rel_l2(got, run_oracle(st, 2, nx, ny, g, 7)) <= 1e-12
 
 
+# a single 1D lattice in FP32 with each two-step launch shape forced (tiles computed from the block
+# index): odd step counts, and step graphs of 8 and 6 steps (6: two two-step launches plus two
+# single steps, so the graph ends on the buffer it starts from)
+@pytest.mark.parametrize("shape", [(64, 4, 2), (128, 2, 2), (64, 2, 2), (256, 1, 2), (64, 1, 1)])
+@pytest.mark.parametrize("L,graph_steps", [(8, 0), (300, 8), (1000, 6), (16384, 32)])
+def test_1d_shapes(shape, L, graph_steps):
+    rng = np.random.default_rng(61 + L)
+    st = I.random_state(rng, L, 1, scale=0.05).astype(np.float32)
+    g = G_SETS[1]
+    lat = qlga.Lattice(1, L, 1, precision=32, g=g)
+    lat.set_1d_shape(*shape)
+    lat.set_graph_steps(graph_steps)
+    lat.load_state(st)
+    n = 2 * graph_steps + 7 if graph_steps else 23
+    lat.step(n)
+    assert lat.shape_1d() == shape
+    got = lat.get_state()
+    lat.close()
+    ref = run_oracle(st, 1, L, 1, g, n)
+    assert rel_l2(got, ref) <= 2e-5
+
+
+def test_1d_shape_errors():
+    lat = qlga.Lattice(2, 64, 16, precision=32, g=G_SETS[1])
+    with pytest.raises(qlga.QlgaError) as e:
+        lat.set_1d_shape(64, 4, 2)
+    assert e.value.status == qlga.QLGA_ERR_UNSUPPORTED
+    lat.close()
+    lat = qlga.Lattice(1, 500, 1, precision=64, g=G_SETS[1])
+    with pytest.raises(qlga.QlgaError) as e:
+        lat.set_1d_shape(64, 4, 2)
+    assert e.value.status == qlga.QLGA_ERR_UNSUPPORTED
+    with pytest.raises(qlga.QlgaError) as e:
+        lat.set_1d_shape(64, 3, 1)
+    assert e.value.status == qlga.QLGA_ERR_INVALID_ARG
+    lat.set_1d_shape(64, 4, 1)
+    assert lat.shape_1d() == (64, 4, 1)
+    lat.set_1d_shape()
+    assert lat.shape_1d() == (0, 0, 0)
+    lat.close()
+
+
 # ------------------------------------------------------------------ observables
 
 @pytest.mark.parametrize("precision", [64, 32])
@@ -456,13 +498,17 @@ def test_fields(precision, ndim):
                                                   (2, 40, 24, 64)])
 def test_step_graphs_give_identical_results(ndim, nx, ny, precision):
     """Small lattices replay runs of fused steps from a captured CUDA graph; the result must be
-    bit-identical to stepping launch by launch, across reads and representation changes."""
+    bit-identical to stepping launch by launch, across reads and representation changes.  A 1D
+    lattice's launch shape is forced (the tuner times graphed and direct launches differently, and
+    the Taylor degree of U is a warp maximum); in FP32 it takes two steps per launch."""
     rng = np.random.default_rng(57 + nx)
     st = I.random_state(rng, nx, ny, scale=0.05)
     g = G_SETS[1]
     outs = []
     for graph_steps in (32, 0):
         lat = qlga.Lattice(ndim, nx, ny, precision=precision, g=g)
+        if ndim == 1:
+            lat.set_1d_shape(*((64, 2, 2) if precision == 32 else (64, 1, 1)))
         lat.set_graph_steps(graph_steps)
         lat.load_state(st)
         lat.step(70)

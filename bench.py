@@ -479,21 +479,25 @@ def run_e2e(lat, state, args, torch, qlga, sites):
     E2E_REPEATS times and the median time is reported (all of them are listed)."""
     host_in = torch.from_numpy(state).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    times = []
+    times, phases = [], []
     for _ in range(E2E_REPEATS):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         qlga.qlga_load_state(lat.handle, host_in.data_ptr(), qlga.QLGA_HOST)
+        t1 = time.perf_counter()
         for i in range(args.steps):
             qlga.qlga_step(lat.handle, 1)
             if args.obs_every and (i + 1) % args.obs_every == 0:
                 qlga.qlga_observables(lat.handle)
+        t2 = time.perf_counter()
         qlga.qlga_get_state(lat.handle, host_out.data_ptr(), qlga.QLGA_HOST)
-        times.append(time.perf_counter() - t0)
+        t3 = time.perf_counter()
+        times.append(t3 - t0)
+        phases.append({"upload_ms": (t1 - t0) * 1e3, "steps_ms": (t2 - t1) * 1e3, "read_back_ms": (t3 - t2) * 1e3})
     dt = sorted(times)[len(times) // 2]
     nbytes = host_in.numel() * host_in.element_size()
     return {"value": sites * args.steps / dt, "unit": UNIT, "seconds": dt,
-            "repeats": [sites * args.steps / t for t in times],
+            "repeats": [sites * args.steps / t for t in times], "phases": phases,
             "h2d_bytes_per_step": nbytes / args.steps,
             "d2h_bytes_per_step": (nbytes + 8 * 16 * (args.steps // max(args.obs_every, 1))) / args.steps,
             "note": "the simulation's input is its state: uploaded once from pinned host memory, "

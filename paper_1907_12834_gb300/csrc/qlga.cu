@@ -439,29 +439,36 @@ inline bool step2d_f32_supported(int64_t nx, int64_t ny) {
            ny <= (int64_t(1) << 30);
 }
 
+// Relative throughput of an SM sub-partition that holds k warps of a fused strip kernel.  FP32:
+// the FMA pipe needs about three warps to stay busy (fitted to the 2D step timed at 256^2 ..
+// 1024^2 with one, two and three warps per sub-partition: 0.67, 0.90, 1); FP64: one warp keeps
+// the FP64 pipe busy (a warp's FP64 FMA holds it for many cycles).
+inline double step2d_pipe_eff(bool fp32, int64_t k) {
+    if (!fp32 || k >= 3) return 1.0;
+    return k == 2 ? 0.90 : 0.67;
+}
+
 // Row chunks per strip.  A chunk of r rows costs about r + w row updates: its first 8 rows only
 // fill the y pipeline and run the kinetic part of a row update, w = 8 x that part (warm10 = 10 w:
 // 32 in FP32, where the kinetic part is ~0.4 of a row update; 18 in FP64, where it is ~0.23).
-// `fill` is the number of warps per SM that keeps the limiting pipe busy (FP32: every resident
-// warp; FP64: one per SM sub-partition, since one FP64 FMA of a warp holds the FP64 pipe for many
-// cycles).  With W = strips x chunks warps the step takes about ceil(W / (sms x fill)) x
-// (ceil(ny / chunks) + w) row times; the chunk count that minimises this, up to the resident
-// capacity sms x per_sm, is used (the larger on ties).
-inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, int fill, int warm10) {
+// With W = strips x chunks warps (at most the resident capacity sms x per_sm) the busiest of the
+// 4 sms sub-partitions holds k = ceil(W / (4 sms)) warps and finishes after about
+// k / eff(k) x (ceil(ny / chunks) + w) row times.  Within one k more chunks are shorter, so the
+// candidates are the largest chunk count of each k; the cheapest is used (the larger on ties).
+inline int step2d_chunks(int64_t strips, int64_t ny, int sms, int per_sm, bool fp32, int warm10) {
     int64_t cmax = (int64_t(sms) * per_sm) / strips;
     if (cmax > ny) cmax = ny;
     if (cmax <= 1) return 1;
-    const int64_t lanes = int64_t(sms) * (fill < 1 ? 1 : fill);
-    // within one wave count the cost falls with the chunk count, so only the largest chunk count
-    // of each wave count is a candidate: c_k = min(cmax, k lanes / strips), k = 1, 2, ...
-    int64_t best = 1, best_cost = -1;
+    const int64_t lanes = 4 * int64_t(sms);
+    int64_t best = 1;
+    double best_cost = -1.0;
     for (int64_t k = 1;; ++k) {
         int64_t c = (k * lanes) / strips;
         if (c > cmax) c = cmax;
         if (c >= 1) {
-            const int64_t waves = (strips * c + lanes - 1) / lanes;
-            const int64_t cost = waves * (10 * ((ny + c - 1) / c) + warm10);  // row times x 10
-            if (best_cost < 0 || cost <= best_cost) {
+            const int64_t kk = (strips * c + lanes - 1) / lanes;
+            const double cost = double(kk) / step2d_pipe_eff(fp32, kk) * (double((ny + c - 1) / c) + 0.1 * warm10);
+            if (best_cost < 0.0 || cost <= best_cost) {
                 best = c;
                 best_cost = cost;
             }
@@ -533,7 +540,7 @@ inline bool step2d_f64_fused_preferred(int64_t nx, int64_t ny) {
     Step2dDevice dv;
     if (step2d_device(&dv)) return true;  // the launch reports the error
     const int64_t strips = nx / kStep2dWarpCols;
-    const int64_t c = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4, 18);
+    const int64_t c = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, false, 18);
     const int64_t lanes = 4 * int64_t(dv.sms);
     const double fused = double((strips * c + lanes - 1) / lanes) * (double((ny + c - 1) / c) + 1.8);
     const double two_pass = 1.135 * double(strips * ny) / double(lanes);
@@ -546,7 +553,7 @@ inline int step2d_f64_launch(const double* in, double* out, int64_t nx, int64_t 
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, 4, 18);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm64, false, 18);
     const int grid = int((strips * chunks + kStep2d64WarpsPerCta - 1) / kStep2d64WarpsPerCta);
     const dim3 b(kStep2d64WarpsPerCta * 32);
     const int smem = kStep2d64SmemBytes;
@@ -567,7 +574,7 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm, dv.per_sm, 32);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm, true, 32);
     const int grid = int((strips * chunks + kStep2dWarpsPerCta - 1) / kStep2dWarpsPerCta);
     const dim3 b(kStep2dWarpsPerCta * 32);
     const int smem = kStep2dWarpSmemBytes;
@@ -606,7 +613,7 @@ inline int obs2d_f32_launch(const float* in, const float* ref, int64_t nx, int64
     Step2dDevice dv;
     if (step2d_device(&dv)) return 1;
     const int64_t strips = nx / kStep2dWarpCols;
-    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm_obs, dv.per_sm_obs, 32);
+    const int chunks = step2d_chunks(strips, ny, dv.sms, dv.per_sm_obs, true, 32);
     const int warps = int(strips * chunks);
     if (obs2d_scratch_bytes(nx, ny, warps) > scratch_bytes) return 2;
     char* p = static_cast<char*>(scratch);

@@ -366,6 +366,21 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     lat.close()
     out["plain_fp64_2d"] = {"lattice": [n, n], "site_updates_per_s": n * n / sec, "ms_per_step": sec * 1e3}
     out["fp32_over_fp64_2d"] = rate_fp32 / out["plain_fp64_2d"]["site_updates_per_s"]
+    # plain 1D single lattices: config 1 (two-soliton scattering, 16384 sites) in FP32 and FP64,
+    # config 0 (bright soliton, 1024 sites) in FP64 -- latency-bound sizes, stepped through graphs
+    def rate_1d(w, precision, steps):
+        lat = qlga.Lattice(1, w.nx, 1, precision=precision, g=w.g, epsilon=w.eps)
+        lat.load_state(w.state.astype(np.float32 if precision == 32 else np.float64))
+        lat.step(100)                                   # shape tuning, graph capture
+        sec = _timed_steps(torch, lat, steps)
+        shape = lat.shape_1d()
+        lat.close()
+        return {"lattice": w.nx, "site_updates_per_s": w.nx / sec, "us_per_step": sec * 1e6,
+                "shape": list(shape)}
+    c1 = inputs.config1()
+    out["config1_fp32_1d"] = rate_1d(c1, 32, 2000)
+    out["config1_fp64_1d"] = rate_1d(c1, 64, 500)
+    out["config0_fp64_1d"] = rate_1d(inputs.config0(), 64, 2000)
     # interleaved FP32 on the bench lattice
     lat = qlga.Lattice(2, n, n, precision=32, g=inputs.CONFIG2_G, interleave=1)
     lat.load_state(state_f32)

@@ -207,12 +207,17 @@ qlga_status qlga_set_graph_steps(qlga_handle* h, int32_t steps);
 qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode);
 qlga_status qlga_get_step2d_kernel(qlga_handle* h, int32_t* kernel);
 
-/* Launch shape of a 1D lattice's steps (the tiled kernel the batches use, tiles computed from the
- * block index): the first fused step times the candidates on the live state and keeps the
- * fastest one-step shape and, in FP32 plain steps, the fastest two-step shape (temporal blocking,
- * see the batches) when it beats it per step; qlga_step then takes fused steps two per launch.
- * qlga_set_1d_shape forces a shape (the list and the (0, 0, 0) reset of qlga_batch_set_shape);
- * qlga_get_1d_shape reports the one fused steps use (zeros before tuning).  Setting waits for the
+/* Launch shape of a 1D lattice's steps: the tiled kernel the batches use (tiles computed from the
+ * block index), or the lane-parallel kernel for small lattices whose one-site-per-thread launches
+ * leave most of the GPU idle: shape (5, 0, 1), a site's five levels on five lanes, six sites per
+ * warp; or (10, 0, 1), the psi and d = a - b recursions of U on separate lanes, three sites per
+ * warp.  The first fused step times the candidates on the live state and keeps the fastest per
+ * step: a one-step shape, in FP32 plain steps a two-step shape (temporal blocking, see the
+ * batches; qlga_step then takes fused steps two per launch), or, in FP64, a lane-parallel kernel
+ * (in FP32 it can be forced: its Taylor degree, a maximum over 3 or 6 sites instead of 32,
+ * truncates closer to the tolerance).
+ * qlga_set_1d_shape forces a shape (the list of qlga_batch_set_shape, (5, 0, 1), (10, 0, 1), or
+ * the (0, 0, 0) reset); qlga_get_1d_shape reports the one fused steps use (zeros before tuning).  Setting waits for the
  * handle's stream and drops captured step graphs.  Errors: QLGA_ERR_UNSUPPORTED on a 2D lattice,
  * or two steps per launch in FP64 or with interleave; QLGA_ERR_INVALID_ARG for another shape. */
 qlga_status qlga_set_1d_shape(qlga_handle* h, int32_t threads, int32_t sites_per_thread, int32_t steps);

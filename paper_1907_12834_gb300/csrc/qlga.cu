@@ -30,6 +30,7 @@
 #include "qlga_obs.cuh"
 #include "qlga_step2d.cuh"
 #include "qlga_batch1d.cuh"
+#include "qlga_lanes1d.cuh"
 #include "qlga_adjoint.cuh"
 #include "qlga_interleave.cuh"
 #include "qlga_step2d_f64.cuh"
@@ -757,6 +758,7 @@ struct qlga_handle {
     int64_t launches;  // kernels launched by this handle
     int tile_cand;  // 1D: launch shape of the tiled step (index into kBatchCands), -1 untuned
     int tile_cand2;  // 1D: two-step shape when it beats tile_cand per step, else -1
+    int tile_lanes;   // 1D: fused steps by the lane-parallel kernel with 5 or 10 lanes per site, 0: not
     int step2d_mode;  // QLGA_STEP2D_AUTO / _FUSED / _TWO_PASS
     // CUDA graphs of graph_steps fused steps starting (and ending) on buffer 0 or 1
     int graph_steps;
@@ -899,15 +901,57 @@ struct EventPair {
     }
 };
 
-// Times the launch shapes on the live state: launch(ci, stream) issues one launch of shape ci on
-// `stream` (writing only work space or the step's output).  The cost compared is the time per
-// step.  Direct: a warm-up launch, then two timed ones on `stream`.  Graphed (where the steps will
-// be replayed from graphs, which hide the host's launch gaps): 4 steps of the shape captured into
-// a graph on a capture stream, one warm-up replay, then two timed replays.  best1 is the fastest
-// one-step shape; best2 the fastest two-step shape if `two_step` allows them and it beats best1
-// per step, else -1.
+// Time per step of one kind of launch on the live state: launch(stream) issues one launch of
+// `steps` fused steps on `stream` (writing only work space or the step's output).  Direct: a
+// warm-up launch, then two timed ones on `stream`.  Graphed (where the steps will be replayed
+// from graphs, which hide the host's launch gaps; such lattices take microseconds per step):
+// kTuneGraphSteps steps captured into a graph on the capture stream cs, one warm-up replay, then
+// three timed replays.
+constexpr int kTuneGraphSteps = 16;
+
 template <class Launch>
-cudaError_t tune_shapes(cudaStream_t stream, bool two_step, bool graphed, Launch&& launch, int* best1, int* best2) {
+cudaError_t time_per_step(cudaStream_t stream, cudaStream_t cs, bool graphed, int steps, EventPair& ev,
+                          Launch&& launch, float* ms_per_step) {
+    cudaError_t e = cudaSuccess;
+    float ms = 0.f;
+    if (graphed) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int k = 0; k < kTuneGraphSteps / steps; ++k) launch(cs);
+            e = cudaStreamEndCapture(cs, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(x, stream);  // warm
+        if (e == cudaSuccess) e = cudaEventRecord(ev.e0, stream);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaGraphLaunch(x, stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+        if (x) cudaGraphExecDestroy(x);
+        *ms_per_step = ms / float(3 * kTuneGraphSteps);
+    } else {
+        launch(stream);  // warm
+        e = cudaEventRecord(ev.e0, stream);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) launch(stream);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
+        *ms_per_step = ms / float(2 * steps);
+    }
+    return e;
+}
+
+// Times the launch shapes of the tiled kernel (launch(ci, stream): one launch of shape ci) with
+// time_per_step and compares the time per step.  best1 is the fastest one-step shape (its time
+// in *t1); best2 the fastest two-step shape if `two_step` allows them and it beats best1 per step,
+// else -1 (*t2 its time, or a large value).
+template <class Launch>
+cudaError_t tune_shapes(cudaStream_t stream, bool two_step, bool graphed, Launch&& launch, int* best1, int* best2,
+                        float* t1_out = nullptr, float* t2_out = nullptr) {
     EventPair ev;
     cudaError_t e = ev.create();
     cudaStream_t cs = nullptr;
@@ -919,34 +963,7 @@ cudaError_t tune_shapes(cudaStream_t stream, bool two_step, bool graphed, Launch
         const int steps = kBatchCands[ci].steps;
         if (steps == 2 && !two_step) continue;
         float ms = 0.f;
-        if (graphed) {
-            cudaGraph_t g = nullptr;
-            cudaGraphExec_t x = nullptr;
-            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                for (int k = 0; k < 4 / steps; ++k) launch(ci, cs);
-                e = cudaStreamEndCapture(cs, &g);
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (e == cudaSuccess) e = cudaGraphLaunch(x, stream);  // warm
-            if (e == cudaSuccess) e = cudaEventRecord(ev.e0, stream);
-            for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaGraphLaunch(x, stream);
-            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
-            if (x) cudaGraphExecDestroy(x);
-            ms /= 8.f;  // two replays of 4 steps
-        } else {
-            launch(ci, stream);  // warm
-            e = cudaEventRecord(ev.e0, stream);
-            for (int k = 0; k < 2 && e == cudaSuccess; ++k) launch(ci, stream);
-            if (e == cudaSuccess) e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaEventRecord(ev.e1, stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(ev.e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e0, ev.e1);
-            ms /= float(2 * steps);
-        }
+        e = time_per_step(stream, cs, graphed, steps, ev, [&](cudaStream_t st) { launch(ci, st); }, &ms);
         if (e != cudaSuccess) break;
         if (steps == 1 && ms < t1) {
             t1 = ms;
@@ -958,6 +975,8 @@ cudaError_t tune_shapes(cudaStream_t stream, bool two_step, bool graphed, Launch
     }
     if (cs) cudaStreamDestroy(cs);
     if (*best2 >= 0 && !(t2 < t1)) *best2 = -1;
+    if (t1_out) *t1_out = t1;
+    if (t2_out) *t2_out = t2;
     return e;
 }
 
@@ -967,30 +986,88 @@ inline int tune_launches(bool two_step, bool graphed) {
     for (int ci = 0; ci < kBatchNumCands; ++ci) {
         const int steps = kBatchCands[ci].steps;
         if (steps == 2 && !two_step) continue;
-        n += graphed ? 3 * (4 / steps) : 3;
+        n += graphed ? 4 * (kTuneGraphSteps / steps) : 3;
     }
     return n;
 }
 
-// 1D: the tiled step kernel (shared with the batches) on the whole lattice, in -> out; `steps`
-// fused steps (2: the two-step shape, which the handle has only in FP32 and when it is faster).
-// The first fused step times the launch shapes on the live state, writing only `out`, and keeps
-// the fastest one-step and two-step shapes.
+// One fused step of a single 1D lattice by the lane-parallel kernel (qlga_lanes1d.cuh) with lps
+// lanes per site (5 or 10).
+template <class T>
+void lanes_1d_launch_t(const TileArgs& a, int lps) {
+    const PotConst<T> pc(a.single_params);
+    const T* in = static_cast<const T*>(a.in);
+    T* out = static_cast<T*>(a.out);
+    const int L = int(a.single_L);
+    const int nb = (L + 30 / lps - 1) / (30 / lps);
+    if (lps == 5) {
+        if (a.variant == 0) k_step1d_lanes<T, 0, 5><<<nb, 32, 0, a.stream>>>(in, out, L, pc, a.status);
+        else k_step1d_lanes<T, 1, 5><<<nb, 32, 0, a.stream>>>(in, out, L, pc, a.status);
+    } else {
+        if (a.variant == 0) k_step1d_lanes<T, 0, 10><<<nb, 32, 0, a.stream>>>(in, out, L, pc, a.status);
+        else k_step1d_lanes<T, 1, 10><<<nb, 32, 0, a.stream>>>(in, out, L, pc, a.status);
+    }
+}
+inline void lanes_1d_launch(const TileArgs& a, int lps) {
+    if (a.precision == 32) lanes_1d_launch_t<float>(a, lps);
+    else lanes_1d_launch_t<double>(a, lps);
+}
+
+// 1D: one fused step (or the kinetic operator alone) of the whole lattice, in -> out; `steps`
+// fused steps (2: the two-step shape of the tiled kernel, which the handle has only in FP32 and
+// when it is faster).  The first fused step times, on the live state and writing only `out`, the
+// tiled kernel's launch shapes (shared with the batches) and the lane-parallel kernel, and keeps
+// the fastest per step; read-outs (pot = false) take the fastest one-step shape of the tiled
+// kernel.
 qlga_status tile_1d(qlga_handle* h, const void* in, void* out, bool pot, int steps = 1) {
     TileArgs a{h->stream, h->cfg.precision, h->cfg.kinetic_variant, pot, in, out, nullptr, 0, nullptr,
                nullptr, h->status, h->cfg.nx, pot_params(h->cfg, 1.0)};
     if (pot && h->tile_cand < 0) {
         const bool two = h->cfg.precision == 32 && !h->cfg.interleave;
         const bool graphed = h->graph_steps > 0;
+        float t1 = 0.f, t2 = 0.f, tl = 0.f;
         cudaError_t e = tune_shapes(h->stream, two, graphed,
                                     [&](int ci, cudaStream_t st) {
                                         TileArgs b = a;
                                         b.stream = st;
                                         tile_step_launch(b, ci);
                                     },
-                                    &h->tile_cand, &h->tile_cand2);
+                                    &h->tile_cand, &h->tile_cand2, &t1, &t2);
+        int lanes = 0;
+        // the lane-parallel kernel, 5 and 10 lanes per site, in FP64 (in FP32 it is no faster, and
+        // its warp-maximum Taylor degree over 3 or 6 sites instead of 32 lets the FP32 truncation,
+        // which accumulates, grow: config 0 after 2000 steps 1.1e-4 against ~1e-5)
+        if (e == cudaSuccess && h->cfg.precision == 64) {
+            EventPair ev;
+            cudaStream_t cs = nullptr;
+            e = ev.create();
+            if (e == cudaSuccess && graphed) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            for (int lps = 5; lps <= 10 && e == cudaSuccess; lps += 5) {
+                e = time_per_step(h->stream, cs, graphed, 1, ev,
+                                  [&](cudaStream_t st) {
+                                      TileArgs b = a;
+                                      b.stream = st;
+                                      lanes_1d_launch(b, lps);
+                                  },
+                                  &tl);
+                if (e == cudaSuccess && tl < t1 && (h->tile_cand2 < 0 || tl < t2)) {
+                    lanes = lps;
+                    t1 = tl;
+                    t2 = tl;
+                }
+            }
+            if (cs) cudaStreamDestroy(cs);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "1D step tuning");
-        h->launches += tune_launches(two, graphed);
+        h->tile_lanes = lanes;
+        if (lanes) h->tile_cand2 = -1;
+        h->launches += tune_launches(two, graphed) + (h->cfg.precision == 64 ? 2 * (graphed ? 4 * kTuneGraphSteps : 3) : 0);
+    }
+    if (pot && steps == 1 && h->tile_lanes) {
+        lanes_1d_launch(a, h->tile_lanes);
+        QLGA_CUDA(cudaGetLastError(), "k_step1d_lanes launch");
+        h->launches += 1;
+        return QLGA_OK;
     }
     const int ci = steps == 2 ? h->tile_cand2 : (h->tile_cand >= 0 ? h->tile_cand : kBatchDefaultCand);
     if (!tile_cand_ok(h->cfg.precision, pot, ci)) return fail(QLGA_ERR_INVALID_ARG, "no launch shape for this 1D step%s");
@@ -1281,6 +1358,7 @@ static qlga_status init_handle(qlga_handle* h, const qlga_config* cfg, void* str
     h->graph[0] = h->graph[1] = nullptr;
     h->tile_cand = -1;
     h->tile_cand2 = -1;
+    h->tile_lanes = 0;
     h->step2d_mode = QLGA_STEP2D_AUTO;
     QLGA_CUDA(cudaMemsetAsync(h->X[0], 0, state_bytes_of(*cfg), h->stream), "state clear");
     QLGA_CUDA(cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream), "status clear");
@@ -1585,7 +1663,10 @@ qlga_status qlga_set_1d_shape(qlga_handle* h, int32_t threads, int32_t sites_per
     if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
     if (h->cfg.ndim != 1) return fail(QLGA_ERR_UNSUPPORTED, "launch shapes are for 1D lattices%s");
     int c1 = -1, c2 = -1;
-    if (threads != 0 || sites_per_thread != 0 || steps != 0) {
+    const int lanes = (threads == 5 || threads == 10) && sites_per_thread == 0 && steps == 1 ? threads : 0;
+    if (lanes) {
+        c1 = kBatchDefaultCand;  // read-outs of the pending state
+    } else if (threads != 0 || sites_per_thread != 0 || steps != 0) {
         const int ci = batch_cand_of(threads, sites_per_thread, steps);
         if (ci < 0) return fail(QLGA_ERR_INVALID_ARG, "not one of the launch shapes%s");
         if (steps == 2 && (h->cfg.precision != 32 || h->cfg.interleave))
@@ -1597,11 +1678,18 @@ qlga_status qlga_set_1d_shape(qlga_handle* h, int32_t threads, int32_t sites_per
     graphs_release(h);
     h->tile_cand = c1;
     h->tile_cand2 = c2;
+    h->tile_lanes = lanes;
     return QLGA_OK;
 }
 
 qlga_status qlga_get_1d_shape(qlga_handle* h, int32_t* threads, int32_t* sites_per_thread, int32_t* steps) {
     if (!h || !threads || !sites_per_thread || !steps) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (h->tile_lanes) {
+        *threads = h->tile_lanes;
+        *sites_per_thread = 0;
+        *steps = 1;
+        return QLGA_OK;
+    }
     const int ci = h->tile_cand2 >= 0 ? h->tile_cand2 : h->tile_cand;
     *threads = ci >= 0 ? kBatchCands[ci].threads : 0;
     *sites_per_thread = ci >= 0 ? kBatchCands[ci].spt : 0;

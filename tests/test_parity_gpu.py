@@ -213,7 +213,8 @@ def test_step_counts_and_pending_representation():
 # a single 1D lattice in FP32 with each two-step launch shape forced (tiles computed from the block
 # index): odd step counts, and step graphs of 8 and 6 steps (6: two two-step launches plus two
 # single steps, so the graph ends on the buffer it starts from)
-@pytest.mark.parametrize("shape", [(64, 4, 2), (128, 2, 2), (64, 2, 2), (256, 1, 2), (64, 1, 1)])
+@pytest.mark.parametrize("shape", [(64, 4, 2), (128, 2, 2), (64, 2, 2), (256, 1, 2), (64, 1, 1), (5, 0, 1),
+                                   (10, 0, 1)])
 @pytest.mark.parametrize("L,graph_steps", [(8, 0), (300, 8), (1000, 6), (16384, 32)])
 def test_1d_shapes(shape, L, graph_steps):
     rng = np.random.default_rng(61 + L)
@@ -230,6 +231,47 @@ def test_1d_shapes(shape, L, graph_steps):
     lat.close()
     ref = run_oracle(st, 1, L, 1, g, n)
     assert rel_l2(got, ref) <= 2e-5
+
+
+# the lane-parallel 1D kernel (a site's levels on five lanes, six sites per warp; or the psi and d
+# recursions of U on separate lanes, ten per site, three sites per warp) in FP64: lengths that
+# leave the last warp partly empty, both collide readings, graphs on and off
+@pytest.mark.parametrize("lps", [5, 10])
+@pytest.mark.parametrize("L", [8, 13, 1024, 3001])
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("graph_steps", [0, 8])
+def test_1d_lanes_fp64(lps, L, variant, graph_steps):
+    rng = np.random.default_rng(71 + L + variant)
+    st = I.random_state(rng, L, 1, scale=0.05)
+    g = G_SETS[variant]
+    lat = qlga.Lattice(1, L, 1, precision=64, g=g, kinetic_variant=variant)
+    lat.set_1d_shape(lps, 0, 1)
+    lat.set_graph_steps(graph_steps)
+    lat.load_state(st)
+    lat.step(25)
+    assert lat.shape_1d() == (lps, 0, 1)
+    got = lat.get_state()
+    lat.close()
+    assert rel_l2(got, run_oracle(st, 1, L, 1, g, 25, variant=variant)) <= 1e-11
+
+
+@pytest.mark.parametrize("lps", [5, 10])
+def test_config0_lanes_full_run_fp64(lps):
+    """Config 0 (row-1 bright soliton, L = 1024) for its 2000 steps with the lane-parallel
+    kernel: parity 1e-11, populations and norm conserved to 1e-12."""
+    w = I.config0()
+    lat = qlga.Lattice(1, w.nx, 1, precision=64, g=w.g, epsilon=w.eps)
+    lat.set_1d_shape(lps, 0, 1)
+    lat.load_state(w.state)
+    o0 = lat.observables()
+    lat.step(w.steps)
+    o1 = lat.observables()
+    got = lat.get_state()
+    lat.close()
+    ref = run_oracle(w.state, 1, w.nx, 1, w.g, w.steps)
+    assert rel_l2(got, ref) <= 1e-11
+    assert abs(o1["norm_qubit"] - o0["norm_qubit"]) <= 1e-12 * o0["norm_qubit"]
+    np.testing.assert_allclose(o1["pop"], o0["pop"], rtol=0, atol=1e-12 * o0["norm_qubit"])
 
 
 def test_1d_shape_errors():

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <limits>
 #include <cuda_runtime.h>
 
 namespace qlga {
@@ -359,9 +360,152 @@ __device__ __forceinline__ void taylor_apply2(const WOp<T>& W, const cpx<T> xp[5
     }
 }
 
+// The Taylor sums in a frame turned about the spin z axis (used by the fused 2D kernels).
+//
+// A rotation about z multiplies level m by e^{i m phi}; it leaves rho, F_z and the singlet
+// relation s_m = (-1)^m conj(psi_{-m}) unchanged (the phase is odd in m) and turns F_+ into
+// e^{-i phi} F_+.  With e = F_+ / |F_+| and x' = diag(e^2, e, 1, conj(e), conj(e)^2) x (index order
+// m = +2..-2), F_+ becomes the real |F_+|, so W's off-diagonal entries are real and each costs two
+// multiply-adds instead of four.  The Taylor polynomial commutes with the (unitary, diagonal)
+// change of frame, so the result is the same polynomial in W; the frame is undone by folding
+// diag(conj(e)^2, conj(e), 1, e, e^2) into the output phase.
+//
+// Each Horner step v <- x - (i/k) W v is one pass: W / k is formed once per k (shared by the two
+// vectors) and x is the start of every output's multiply-add chain, so the step costs no
+// operations beyond the matrix-vector product.
+template <class T>
+struct WFrameK {
+    T D[5];    // diagonal of W / k
+    T e0, e1;  // off-diagonal entries of W / k: (0,1) = (3,4) = e0, (1,2) = (2,3) = e1 (real)
+    T R;       // singlet coefficient of W / k
+};
+
+template <class T>
+__device__ __forceinline__ void horner_zframe(const cpx<T> x[5], const cpx<T> v[5], cpx<T> o[5], const WFrameK<T>& Wk,
+                                              const cpx<T> u[5]) {
+    cpx<T> t0 = cmul(u[0], v[0]), t1 = cmul(u[1], v[1]);
+    t0 = cfma(u[2], v[2], t0);
+    t1 = cfma(u[3], v[3], t1);
+    t0 = cfma(u[4], v[4], t0);
+    const cpx<T> t = Wk.R * (t0 + t1);  // (s^dagger v) times the singlet coefficient
+    // y_i = D_i v_i + conj(u_i) t + (off-diagonal neighbours); o = x - i y:
+    // o.re = x.re + y.im, o.im = x.im - y.re
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        T re = fma(Wk.D[i], v[i].im, x[i].re);
+        T im = fma(-Wk.D[i], v[i].re, x[i].im);
+        re = fma(u[i].re, t.im, re);
+        re = fma(-u[i].im, t.re, re);
+        im = fma(-u[i].re, t.re, im);
+        im = fma(-u[i].im, t.im, im);
+        if (i > 0) {
+            const T c = (i == 1 || i == 4) ? Wk.e0 : Wk.e1;
+            re = fma(c, v[i - 1].im, re);
+            im = fma(-c, v[i - 1].re, im);
+        }
+        if (i < 4) {
+            const T c = (i == 0 || i == 3) ? Wk.e0 : Wk.e1;
+            re = fma(c, v[i + 1].im, re);
+            im = fma(-c, v[i + 1].re, im);
+        }
+        o[i] = {re, im};
+    }
+}
+
+// The end of potential_site in the z frame: the Taylor sums of exp(-i delta W) on psi (degree K) and d
+// (degree Kd <= K) in the z frame, then a = U(psi + d)/2, b = U(psi - d)/2.  Fp = F_+ and the
+// other inputs as in potential_site.
+template <class T>
+__device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], const cpx<T> psi[5], const cpx<T> d[5],
+                                                      cpx<T> Fp, T rho, T Fz, int K, int Kd, const PotConst<T>& C,
+                                                      T inv_sigma2, T out_scale) {
+    const T fp2 = norm2(Fp);
+    cpx<T> e = {T(1), T(0)};
+    T fpa = T(0);  // |F_+|; below the smallest normal number it is taken as 0 (its terms are far below rounding)
+    if (fp2 > std::numeric_limits<T>::min()) {
+        const T r = rsqrt(fp2);
+        e = r * Fp;
+        fpa = fp2 * r;
+    }
+    const cpx<T> e2 = cmul(e, e);
+    cpx<T> xp[5], xd[5];
+    xp[0] = cmul(e2, psi[0]);
+    xp[1] = cmul(e, psi[1]);
+    xp[2] = psi[2];
+    xp[3] = cmulc(e, psi[3]);
+    xp[4] = cmulc(e2, psi[4]);
+    xd[0] = cmul(e2, d[0]);
+    xd[1] = cmul(e, d[1]);
+    xd[2] = d[2];
+    xd[3] = cmulc(e, d[3]);
+    xd[4] = cmulc(e2, d[4]);
+    cpx<T> u[5];  // u_j = (-1)^{m_j} psi'_{4-j} = conj(s'_j)
+    u[0] = xp[4];
+    u[1] = {-xp[3].re, -xp[3].im};
+    u[2] = xp[2];
+    u[3] = {-xp[1].re, -xp[1].im};
+    u[4] = xp[0];
+    const T g2r = C.dr * rho, gz = C.dz * Fz;
+    const T D[5] = {T(2) * gz - g2r, gz - g2r, -g2r, -gz - g2r, T(-2) * gz - g2r};
+    const T ep0 = C.e0 * fpa, ep1 = C.e1 * fpa, R = C.R * inv_sigma2;
+    cpx<T> vp[5], vd[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        vp[i] = xp[i];
+        vd[i] = xd[i];
+    }
+    auto scaled = [&](int k) {
+        const T ik = inv_k(k, T(0));
+        WFrameK<T> Wk;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Wk.D[i] = D[i] * ik;
+        Wk.e0 = ep0 * ik;
+        Wk.e1 = ep1 * ik;
+        Wk.R = R * ik;
+        return Wk;
+    };
+    int k = K;
+    for (; k > Kd; --k) {
+        const WFrameK<T> Wk = scaled(k);
+        cpx<T> op[5];
+        horner_zframe(xp, vp, op, Wk, u);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) vp[i] = op[i];
+    }
+    for (; k >= 1; --k) {
+        const WFrameK<T> Wk = scaled(k);
+        cpx<T> op[5], od[5];
+        horner_zframe(xp, vp, op, Wk, u);
+        horner_zframe(xd, vd, od, Wk, u);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            vp[i] = op[i];
+            vd[i] = od[i];
+        }
+    }
+    T sn, cs;
+    sin_cos(C.cphase * rho, &sn, &cs);
+    const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
+    cpx<T> q[5];  // the output phase with the frame undone
+    q[0] = cmulc(e2, ph);
+    q[1] = cmulc(e, ph);
+    q[2] = ph;
+    q[3] = cmul(e, ph);
+    q[4] = cmul(e2, ph);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        a[i] = cmul(q[i], vp[i] + vd[i]);
+        b[i] = cmul(q[i], vp[i] - vd[i]);
+    }
+}
+
 // Apply U to the pair (a, b) of one site in place.  SPLIT_D: pick the degree for d = a - b
-// from its size relative to psi (FP32); otherwise d uses the degree of psi.
-template <class T, bool SPLIT_D>
+// from its size relative to psi (FP32); otherwise d uses the degree of psi.  ZFRAME: run the
+// Taylor sums in the z frame (potential_tail_zframe).  The frame costs a fixed ~60 operations per
+// site and saves ~26 per vector and Taylor term, so it pays where the warp-uniform degree is about
+// 3 or more (the 2D vortex states of the fused warp-strip kernels: 2.4% faster at 4096^2) and
+// not at the lower degrees of the 1D workloads (5% slower there).
+template <class T, bool SPLIT_D, bool ZFRAME = false>
 __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotConst<T>& C,
                                                T inv_sigma2, T out_scale, unsigned* status) {
     cpx<T> psi[5], d[5];
@@ -399,6 +543,10 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
             term *= beta * inv_k(k + 1, T(0));
         }
         Kd = warp_max_int(k);
+    }
+    if constexpr (ZFRAME) {
+        potential_tail_zframe<T>(a, b, psi, d, Fp, rho, Fz, K, Kd, C, inv_sigma2, out_scale);
+        return;
     }
     WOp<T> W;
     const T g2r = C.dr * rho;

@@ -163,6 +163,16 @@ def recorded_step_counters():
     return d if d.get("kernel_source_hash") == kernel_source_hash() else None
 
 
+def counters_note():
+    """One line from the committed ncu figures of the fused step, if they match the source."""
+    d = recorded_step_counters()
+    if d is None:
+        return "no ncu figure for the current kernel source"
+    return "FMA pipe %.0f%% busy, %.1f DRAM bytes per site against %d algorithmic" % (
+        100 * float(d["fma_pipe_busy_frac"]), float(d["dram_bytes_per_site"]),
+        int(d["algorithmic_bytes_per_site"]))
+
+
 def alu_roofline(sites, kernel_ms, sms):
     """FP32 FMA-pipe view of the fused step: issue cycles per site from the ncu capture, over the
     live launch duration, against one FMA-pipe issue per SM sub-partition per cycle at the maximum
@@ -322,8 +332,8 @@ def run_gb300(args):
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
                      "note": "the fused step is limited by FP32 FMA-pipe cycles of the potential "
-                             "(ncu on the settled state: FMA pipe 61% busy, DRAM 36%; "
-                             "profiles/step2d_f32_2048_full.md), not by HBM traffic"},
+                             "(ncu on the settled state: %s; profiles/step2d_f32_2048_full.md), "
+                             "not by HBM traffic" % counters_note()},
         "alu": alu_roofline(sites, kernel_ms, torch.cuda.get_device_properties(0).multi_processor_count),
         "e2e": e2e,
         "drift": drift,

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
 #pragma unroll
             for (int m = 0; m < 5; ++m) a[m] = b[m] = {T(0), T(0)};
         }
-        potential_site<T, SPLIT>(a, b, PC, T(1), T(0.5), status);
+        potential_site<T, SPLIT, kZframe64<T>>(a, b, PC, T(1), T(0.5), status);
         if (active) SiteIO<T>::store(X, nsites, site, a, b);
     }
 }
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
             oa[m] = {sc * acc_a.re, sc * acc_a.im};
             ob[m] = {sc * acc_bt.im, -sc * acc_bt.re};  // b = -i bt
         }
-        if (POT) potential_site<T, std::is_same<T, float>::value>(oa, ob, PC, T(1), T(0.5), status);
+        if (POT) potential_site<T, std::is_same<T, float>::value, kZframe64<T>>(oa, ob, PC, T(1), T(0.5), status);
         if (active) SiteIO<T>::store(out, nsites, site, oa, ob);
     }
 }
@@ -2066,7 +2066,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchT
             b[m] = {p.v[3], -p.v[2]};
         }
         const PotConst<T> C = consts[tile.run];
-        potential_site<T, sizeof(T) == 4>(a, b, C, T(1), T(0.5), status);
+        potential_site<T, sizeof(T) == 4, kZframe64<T>>(a, b, C, T(1), T(0.5), status);
         __syncwarp();
         if (j < run.L) {
 #pragma unroll

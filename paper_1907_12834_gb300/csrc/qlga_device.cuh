@@ -15,6 +15,7 @@
 
 #include <cstdint>
 #include <limits>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace qlga {
@@ -499,12 +500,19 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
     }
 }
 
+// FP64 kernels run the Taylor sums in the z frame too: with the FP64 tolerance the degree is
+// higher, and the frame made the fused and two-pass FP64 2D steps 9% faster (the interleaved
+// passes keep the plain form: more spills there).
+template <class T>
+constexpr bool kZframe64 = std::is_same<T, double>::value;
+
 // Apply U to the pair (a, b) of one site in place.  SPLIT_D: pick the degree for d = a - b
 // from its size relative to psi (FP32); otherwise d uses the degree of psi.  ZFRAME: run the
 // Taylor sums in the z frame (potential_tail_zframe).  The frame costs a fixed ~60 operations per
 // site and saves ~26 per vector and Taylor term, so it pays where the warp-uniform degree is about
-// 3 or more (the 2D vortex states of the fused warp-strip kernels: 2.4% faster at 4096^2) and
-// not at the lower degrees of the 1D workloads (5% slower there).
+// 3 or more: the FP32 2D vortex states of the fused warp-strip kernels (2.4% faster at 4096^2)
+// and every FP64 kernel (kZframe64), but not the lower FP32 degrees of the 1D workloads (5%
+// slower there).
 template <class T, bool SPLIT_D, bool ZFRAME = false>
 __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotConst<T>& C,
                                                T inv_sigma2, T out_scale, unsigned* status) {

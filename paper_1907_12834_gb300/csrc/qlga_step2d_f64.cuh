@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kStep2d64WarpsPerCta * 32)
         }
         if (r >= 8) {  // pipeline full: this is output row y_begin + r - 8
             if (POT) {
-                potential_site<double, false>(oa, ob, PC, 1.0 / 65536.0, 0.5 / 256.0, status);
+                potential_site<double, false, kZframe64<double>>(oa, ob, PC, 1.0 / 65536.0, 0.5 / 256.0, status);
             } else {
 #pragma unroll
                 for (int m = 0; m < 5; ++m) {

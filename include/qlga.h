@@ -55,7 +55,8 @@ typedef enum qlga_status {
     QLGA_ERR_INVALID_ARG = 1,   /* a NULL pointer, a bad size, a bad enum value              */
     QLGA_ERR_OOM = 2,           /* cudaMalloc failed                                          */
     QLGA_ERR_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed              */
-    QLGA_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (status word set by a kernel) */
+    QLGA_ERR_TIMEOUT = 4,       /* reserved for a bounded device wait that gives up; no kernel of this
+                                   library waits on another CTA or on the host, so none returns it */
     QLGA_ERR_NOT_FINITE = 5,    /* the state holds NaN or Inf                                 */
     QLGA_ERR_UNSUPPORTED = 6    /* a valid configuration that this build does not implement   */
 } qlga_status;

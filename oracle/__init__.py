@@ -23,6 +23,8 @@ Parity status of each function (what pins it; see tests/test_oracle_pins.py):
   vjp_kinetic       pinned: dot-product identity <K v, w> = <v, K^dagger w>, K^dagger K = 1.
   vjp_potential /   pinned: central finite differences of the (pinned) forward operators in
   vjp_step / run    random directions, coupling derivatives by finite differences in g.
+  step_long_double  not a pin: the same source built in long double, which bounds the FP64
+                    oracle's own rounding (tests/test_oracle_precision.py).
 
 Adjoint cotangents: for a real loss L the cotangent array has the state's shape and holds
 dL/d(each real component); dL = sum(cot * dx).
@@ -65,6 +67,74 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+_LIB_LD = os.path.join(_HERE, "liboracle_ld.so")
+
+# Appended to the long-double source: a float64 state in, nsteps in extended precision, one
+# rounding to float64 on the way out.
+_LD_ENTRY = r"""
+int oracle_step_from_double(const double* in, double* out, const oracle_cfg_f64* c, long nsteps,
+                            int nthreads) {
+    const long n = 5 * c->nx * c->ny * 4;
+    long double* st = (long double*)malloc(sizeof(long double) * (size_t)n);
+    if (!st) return 2;
+    for (long i = 0; i < n; ++i) st[i] = in[i];
+    oracle_cfg cfg = {c->ndim, c->nx, c->ny, c->g0, c->g1, c->g2, c->interleave, c->kinetic_variant};
+    const int rc = oracle_step(st, &cfg, nsteps, nthreads);
+    for (long i = 0; i < n; ++i) out[i] = (double)st[i];
+    free(st);
+    return rc;
+}
+"""
+
+
+def long_double_source(src_text: str = None) -> str:
+    """The oracle's C source with every `double` made `long double` and the math calls made
+    type-generic (<tgmath.h>), plus the entry point oracle_step_from_double.  It is the same
+    algorithm evaluated with a longer significand (64 bits on x86-64, 113 on aarch64), used only
+    to measure how far the FP64 oracle's own rounding carries it.  Constants the source computes
+    from double arguments (sqrt(1.5) of the spin matrices) stay the FP64 values, so both builds
+    evaluate the same discrete operator."""
+    import re
+
+    src = open(_SRC).read() if src_text is None else src_text
+    head = "#include <complex.h>\n#include <math.h>\n"
+    if head not in src or "long double" in src:
+        raise ValueError("unexpected oracle source layout")
+    src = src.replace(head, "#include <tgmath.h>\n", 1)
+    cfg_f64 = src[src.index("typedef struct oracle_cfg {"):src.index("} oracle_cfg;") + len("} oracle_cfg;")]
+    cfg_f64 = cfg_f64.replace("oracle_cfg {", "oracle_cfg_f64 {").replace("} oracle_cfg;", "} oracle_cfg_f64;")
+    src = re.sub(r"\bdouble\b", "long double", src)
+    return src + "\n" + cfg_f64 + "\n" + _LD_ENTRY
+
+
+def build_long_double(force: bool = False) -> str:
+    """Compile long_double_source() into liboracle_ld.so (gcc, -O2, OpenMP)."""
+    if not force and os.path.exists(_LIB_LD) and os.path.getmtime(_LIB_LD) >= os.path.getmtime(_SRC):
+        return _LIB_LD
+    tmp = _LIB_LD + ".%d.tmp" % os.getpid()
+    src = tmp + ".c"
+    with open(src, "w") as f:
+        f.write(long_double_source())
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"],
+                   check=True)
+    os.remove(src)
+    os.replace(tmp, _LIB_LD)
+    return _LIB_LD
+
+
+def step_long_double(state: np.ndarray, cfg: OracleCfg, nsteps: int, nthreads: int = 0) -> np.ndarray:
+    """A copy of `state` advanced nsteps QLGA steps by the long-double build of the oracle."""
+    _check_state(state, cfg)
+    lib = ctypes.CDLL(build_long_double())
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_step_from_double.argtypes = [dp, dp, ctypes.POINTER(OracleCfg), ctypes.c_long, ctypes.c_int]
+    lib.oracle_step_from_double.restype = ctypes.c_int
+    out = np.empty_like(state)
+    if lib.oracle_step_from_double(_dptr(state), _dptr(out), ctypes.byref(cfg), int(nsteps), int(nthreads)):
+        raise ValueError("oracle_step_from_double rejected its arguments")
+    return out
 
 
 def compile_source(src_text: str, out_path: str) -> str:

@@ -361,7 +361,8 @@ __device__ __forceinline__ void taylor_apply2(const WOp<T>& W, const cpx<T> xp[5
     }
 }
 
-// The Taylor sums in a frame turned about the spin z axis (used by the fused 2D kernels).
+// The Taylor sums in a frame turned about the spin z axis (used by the fused 2D FP32 kernels and
+// by the FP64 kernels outside the interleaved passes).
 //
 // A rotation about z multiplies level m by e^{i m phi}; it leaves rho, F_z and the singlet
 // relation s_m = (-1)^m conj(psi_{-m}) unchanged (the phase is odd in m) and turns F_+ into
@@ -511,8 +512,8 @@ constexpr bool kZframe64 = std::is_same<T, double>::value;
 // Taylor sums in the z frame (potential_tail_zframe).  The frame costs a fixed ~60 operations per
 // site and saves ~26 per vector and Taylor term, so it pays where the warp-uniform degree is about
 // 3 or more: the FP32 2D vortex states of the fused warp-strip kernels (2.4% faster at 4096^2)
-// and every FP64 kernel (kZframe64), but not the lower FP32 degrees of the 1D workloads (5%
-// slower there).
+// and the FP64 kernels that call this function outside the interleaved passes (kZframe64), but
+// not the lower FP32 degrees of the 1D workloads (5% slower there).
 template <class T, bool SPLIT_D, bool ZFRAME = false>
 __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const PotConst<T>& C,
                                                T inv_sigma2, T out_scale, unsigned* status) {

@@ -40,3 +40,10 @@ def test_stale_counters_are_reported_as_null(monkeypatch):
     alu = bench.alu_roofline(4096 * 4096, 0.86, 152)
     assert alu["achieved"] is None and alu["frac"] is None
     assert "no ncu figure" in bench.counters_note()
+
+
+def test_source_hash_ignores_comments_only():
+    code = "int f(int x) {\n    return x + 1;  // one more\n}\n/* block\n   comment */\n"
+    assert bench.strip_comments(code) == bench.strip_comments(code.replace("one more", "plus one"))
+    assert bench.strip_comments(code) == bench.strip_comments("// header\n" + code)
+    assert bench.strip_comments(code) != bench.strip_comments(code.replace("x + 1", "x + 2"))

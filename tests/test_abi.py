@@ -61,3 +61,62 @@ def test_status_strings(lib):
     for s in range(7):
         assert qlga.qlga_status_string(s)
     assert qlga.qlga_status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(lengths=[]), qlga.QLGA_ERR_INVALID_ARG),                              # empty batch
+    (dict(lengths=[64, 7]), qlga.QLGA_ERR_INVALID_ARG),                         # run below 8 sites
+    (dict(lengths=[(1 << 30) + 1]), qlga.QLGA_ERR_INVALID_ARG),                 # 1D run above 2^30
+    (dict(lengths=[1 << 30] * 17), qlga.QLGA_ERR_INVALID_ARG),                  # batch above 2^34 sites
+    (dict(lengths=[40], heights=[16]), qlga.QLGA_ERR_INVALID_ARG),              # 2D nx not a multiple of 32
+    (dict(lengths=[64], heights=[4]), qlga.QLGA_ERR_INVALID_ARG),               # 2D ny below 8
+    (dict(lengths=[64], heights=[16], precision=64), qlga.QLGA_ERR_UNSUPPORTED),  # 2D runs are FP32 only
+    (dict(lengths=[64], g=[(float("nan"), 0.0, 0.0)]), qlga.QLGA_ERR_INVALID_ARG),
+    (dict(lengths=[64], kinetic_variant=5), qlga.QLGA_ERR_INVALID_ARG),
+    (dict(lengths=[64], precision=16), qlga.QLGA_ERR_INVALID_ARG),
+])
+def test_invalid_batches_rejected_before_any_device_call(lib, kw, status):
+    kw = dict(kw)
+    lengths = kw.pop("lengths")
+    g = kw.pop("g", [(1.0, 0.1, 0.2)] * len(lengths))
+    cfg, keep = qlga.make_batch_config(lengths, g, **kw)
+    with pytest.raises(qlga.QlgaError) as ei:
+        qlga.qlga_batch_state_bytes(cfg)
+    assert ei.value.status == status
+    h = ctypes.c_void_p()
+    assert lib.qlga_batch_create(ctypes.byref(cfg), None, ctypes.byref(h)) == status
+    assert not h.value
+    del keep
+
+
+def test_batch_state_bytes(lib):
+    cfg, keep = qlga.make_batch_config([64, 100, 64], [(1.0, 0.1, 0.2)] * 3, heights=[1, 1, 16])
+    assert qlga.qlga_batch_state_bytes(cfg) == 80 * (64 + 100 + 64 * 16)
+    cfg, keep = qlga.make_batch_config([8, 4096], [(1.0, 0.1, 0.2)] * 2, precision=64)
+    assert qlga.qlga_batch_state_bytes(cfg) == 160 * (8 + 4096)
+
+
+def test_create_rejects_bad_arguments_before_allocating(lib):
+    h = ctypes.c_void_p()
+    bad = qlga.make_config(1, 4)
+    assert lib.qlga_create(ctypes.byref(bad), None, ctypes.byref(h)) == qlga.QLGA_ERR_INVALID_ARG
+    assert not h.value
+    good = qlga.make_config(1, 64)
+    assert lib.qlga_create(ctypes.byref(good), None, None) == qlga.QLGA_ERR_INVALID_ARG
+
+
+def test_adjoint_workspace_bytes(lib):
+    """Work space of a checkpointed adjoint run: four state-sized buffers, one checkpoint per
+    C steps and a segment of up to C recomputed states, plus a fixed block of partial sums."""
+    cfg = qlga.make_config(2, 512, 512, precision=32)
+    state = qlga.qlga_state_bytes(cfg)      # a multiple of 256: no alignment padding between states
+    fixed = set()
+    for n, c in ((200, 100), (200, 50), (200, 200), (200, 1), (1, 1), (0, 5), (25, 7)):
+        nck = -(-n // c) if n > 0 else 0
+        slots = min(c, n) if n > 0 else 1
+        fixed.add(qlga.qlga_adjoint_workspace_bytes(cfg, n, c) - state * (4 + nck + slots))
+    assert len(fixed) == 1 and 0 < fixed.pop() < (1 << 20)
+    for nsteps, every in ((-1, 10), (10, 0)):
+        with pytest.raises(qlga.QlgaError) as ei:
+            qlga.qlga_adjoint_workspace_bytes(cfg, nsteps, every)
+        assert ei.value.status == qlga.QLGA_ERR_INVALID_ARG

@@ -311,6 +311,38 @@ def obs_to_dict(o: QlgaObs) -> dict:
     return d
 
 
+# ------------------------------------------------------------------ buffer checks
+#
+# The library reads or writes the whole extent of a buffer through a raw pointer, so a buffer of
+# the wrong size, type or device would be read or written past its end.  These checks run before
+# every such call of the classes below (and are not asserts, which `python -O` removes).
+
+def require_device_tensor(t, shape, dtype, device, what, writable=False):
+    """Raise unless `t` is a CUDA tensor of `shape` and `dtype` on `device` (contiguous when the
+    library writes into it)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must be %s of shape %s, got %s of shape %s"
+                         % (what, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+    if t.device.index != device.index:
+        raise ValueError("%s is on %s, the lattice on %s" % (what, t.device, device))
+    if writable and not t.is_contiguous():
+        raise ValueError("%s must be contiguous: the library writes into it" % what)
+    return t
+
+
+def require_host_array(a, shape, dtype, what, writable=False):
+    """Raise unless `a` is a C-contiguous numpy array of `shape` and `dtype` (writeable when the
+    library writes into it)."""
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or a.shape != tuple(shape):
+        raise ValueError("%s must be a numpy array of %s and shape %s" % (what, np.dtype(dtype), tuple(shape)))
+    if not a.flags.c_contiguous or (writable and not a.flags.writeable):
+        raise ValueError("%s must be C-contiguous%s" % (what, " and writeable" if writable else ""))
+    return a
+
+
 # ------------------------------------------------------------------ high-level lattice
 
 class Lattice:
@@ -329,6 +361,8 @@ class Lattice:
         self.dtype = np.float32 if precision == 32 else np.float64
         self.tdtype = torch.float32 if precision == 32 else torch.float64
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
         self.device = dev
         sb = qlga_state_bytes(self.cfg)
         wb = qlga_workspace_bytes(self.cfg)
@@ -355,12 +389,10 @@ class Lattice:
             if not state.is_cuda:
                 state = state.numpy()
             else:
-                t = state.contiguous()
-                assert t.dtype == self.tdtype and tuple(t.shape) == self.shape
+                t = require_device_tensor(state, self.shape, self.tdtype, self.device, "state").contiguous()
                 qlga_load_state(self.handle, t.data_ptr(), QLGA_DEVICE)
                 return
-        a = np.ascontiguousarray(state, dtype=self.dtype)
-        assert a.shape == self.shape, (a.shape, self.shape)
+        a = require_host_array(np.ascontiguousarray(state, dtype=self.dtype), self.shape, self.dtype, "state")
         qlga_load_state(self.handle, a.ctypes.data, QLGA_HOST)
 
     def load_boson(self, psi):
@@ -373,9 +405,13 @@ class Lattice:
         """Copy of the current state: numpy (host) by default, or into a device tensor."""
         torch = self._torch
         if out is not None and isinstance(out, torch.Tensor) and out.is_cuda:
+            require_device_tensor(out, self.shape, self.tdtype, self.device, "out", writable=True)
             qlga_get_state(self.handle, out.data_ptr(), QLGA_DEVICE)
             return out
-        host = np.empty(self.shape, dtype=self.dtype) if out is None else out
+        if out is None:
+            host = np.empty(self.shape, dtype=self.dtype)
+        else:
+            host = require_host_array(out, self.shape, self.dtype, "out", writable=True)
         qlga_get_state(self.handle, host.ctypes.data, QLGA_HOST)
         return host
 
@@ -397,6 +433,7 @@ class Lattice:
     def observables(self, ref=None) -> dict:
         ref_ptr = 0
         if ref is not None:
+            ref = require_device_tensor(ref, self.shape, self.tdtype, self.device, "ref").contiguous()
             ref_ptr = ref.data_ptr()
         return obs_to_dict(qlga_observables(self.handle, ref_ptr))
 
@@ -414,9 +451,7 @@ class Lattice:
         return self._torch.empty(nb + 256, dtype=self._torch.uint8, device=self.device), nb
 
     def _device_tensor(self, t):
-        assert isinstance(t, self._torch.Tensor) and t.is_cuda, "device tensor expected"
-        assert t.dtype == self.tdtype and tuple(t.shape) == self.shape, (t.dtype, t.shape)
-        return t.contiguous()
+        return require_device_tensor(t, self.shape, self.tdtype, self.device, "tensor").contiguous()
 
     def adjoint_forward(self, x0, nsteps, checkpoint_every, ws):
         """Load x0 (device tensor), run nsteps plain steps keeping checkpoints in ws."""
@@ -668,7 +703,8 @@ class Batch:
 
     def load_state(self, state):
         a = np.ascontiguousarray(state, dtype=self.dtype).ravel()
-        assert a.size == self.nreals
+        if a.size != self.nreals:
+            raise ValueError("batch state must hold %d reals, got %d" % (self.nreals, a.size))
         _check(load_library().qlga_batch_load_state(_H(self.handle), _VP(a.ctypes.data), QLGA_HOST),
                "qlga_batch_load_state")
 

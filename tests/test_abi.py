@@ -120,3 +120,25 @@ def test_adjoint_workspace_bytes(lib):
         with pytest.raises(qlga.QlgaError) as ei:
             qlga.qlga_adjoint_workspace_bytes(cfg, nsteps, every)
         assert ei.value.status == qlga.QLGA_ERR_INVALID_ARG
+
+
+def test_buffer_checks_of_the_binding():
+    """The binding refuses buffers the library would read or write past: wrong dtype, shape,
+    layout, a read-only output, or a host tensor where a device tensor is required."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    shape = (5, 3, 8, 2, 2)
+    ok = np.zeros(shape, np.float32)
+    assert qlga.require_host_array(ok, shape, np.float32, "x", writable=True) is ok
+    bad = [np.zeros(shape, np.float64), np.zeros((5, 3, 9, 2, 2), np.float32),
+           np.zeros((5, 8, 3, 2, 2), np.float32).transpose(0, 2, 1, 3, 4)]
+    for a in bad:
+        with pytest.raises(ValueError):
+            qlga.require_host_array(a, shape, np.float32, "x")
+    ro = np.zeros(shape, np.float32)
+    ro.setflags(write=False)
+    qlga.require_host_array(ro, shape, np.float32, "x")
+    with pytest.raises(ValueError):
+        qlga.require_host_array(ro, shape, np.float32, "x", writable=True)
+    with pytest.raises(TypeError):
+        qlga.require_device_tensor(torch.zeros(shape), shape, torch.float32, torch.device("cuda", 0), "x")

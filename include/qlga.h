@@ -14,7 +14,7 @@
  * State layout ("qubit-pair planes").  Every state buffer, on the host or on the device,
  * holds 5 planes, one per Zeeman level m = +2, +1, 0, -1, -2 (in that order).  A plane
  * holds ny*nx sites, x fastest.  A site holds the two qubit amplitudes of that level
- * (Sec. IV.B, Eq. full_state: two qubits per m_f) as four reals:
+ * (Sec. III.B, Eq. full_state: two qubits per m_f) as four reals:
  *
  *     a.re, a.im, b.re, b.im        (a = first qubit of the pair, b = second)
  *
@@ -84,7 +84,7 @@ typedef struct qlga_config {
 } qlga_config;
 
 /* Global observables of the boson field psi = a + b at the current time (FP64 sums).
- * Sec. IV.A characteristics (Eq. cmap), Sec. IV.C discrete energy (Eq. disecrete_energy). */
+ * Sec. III.B characteristics (Eq. cmap), Sec. IV.B discrete energy (Eq. disecrete_energy). */
 typedef struct qlga_obs {
     double norm_qubit;        /* sum |a|^2 + |b|^2 over sites and levels (exactly conserved) */
     double norm_boson;        /* sum |psi|^2                                                 */
@@ -143,10 +143,10 @@ qlga_status qlga_apply_kinetic(qlga_handle* h);
 
 /* Global observables of the current state; waits for the stream.  `ref_state_device` may
  * be NULL; otherwise it is a device state of the same shape and precision and the overlap
- * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.C). */
+ * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.B). */
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
 
-/* Per-site diagnostic fields of the current state (Sec. IV.A Eq. cmap and Eq. colormap,
+/* Per-site diagnostic fields of the current state (Sec. III.B Eq. cmap and Eq. colormap,
  * Sec. VI.B Eqs. velocity / pointwise_vorticity), written to `dst` as 11 planes of ny*nx
  * values in the handle's precision, x fastest:
  *   0 F_par = sum_m m |psi_m|^2          1 F_perp = |psi^dagger (f_x + i f_y) psi|

@@ -10,7 +10,7 @@
  *
  * State layout (same as the library's data format): 5 planes m = +2..-2, each ny*nx sites
  * with x fastest, each site (a.re, a.im, b.re, b.im): element (m, site, q, c) at
- * ((m*nsites + site)*2 + q)*2 + c.  a = qubit 1 of the pair, b = qubit 2 (Sec. IV.B, Eq.
+ * ((m*nsites + site)*2 + q)*2 + c.  a = qubit 1 of the pair, b = qubit 2 (Sec. III.B, Eq.
  * full_state: two qubits per m_f level).
  *
  * Readings of passages the paper leaves open (the same ones the library documents):
@@ -487,7 +487,7 @@ static void vjp_step(const double* x, double* cot, const oracle_cfg* cfg, double
 
 /* ---------------------------------------------------------------- observables */
 
-/* Sums over the lattice of the boson field psi = a + b (Sec. IV.A Eq. cmap, Sec. IV.C Eq.
+/* Sums over the lattice of the boson field psi = a + b (Sec. III.B Eq. cmap, Sec. IV.B Eq.
  * disecrete_energy); out[] order:
  *  0 norm_qubit  1 norm_boson  2..6 pop[m=+2..-2]  7 magnetisation  8 energy
  *  9 singlet_re  10 singlet_im  11 sum |psi^T J psi|^2  12 sum rho^2

@@ -5,7 +5,7 @@
 // reporting) and the generic kernels:
 //   k_potential      U = exp(-i delta V(psi)) on every site, in place            (Sec. VII.B)
 //   k_kinetic_axis   one axis of the kinetic operator, optionally followed by U  (Sec. VII.B)
-//   k_observables    FP64 sums of Sec. IV.A / IV.C, two-level deterministic reduction
+//   k_observables    FP64 sums of Sec. III.B / IV.B, two-level deterministic reduction
 // The fused 2D FP32 step (one HBM read and one write of the state per step) is in
 // qlga_step2d.cuh.
 //

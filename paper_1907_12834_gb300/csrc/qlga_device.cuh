@@ -589,9 +589,9 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
 
 // ------------------------------------------------------------------ observables
 //
-// Per-site terms of the boson field psi = a + b, accumulated in FP64 (Sec. IV.A Eq. cmap; the
+// Per-site terms of the boson field psi = a + b, accumulated in FP64 (Sec. III.B Eq. cmap; the
 // energy density is the functional whose variation is V(psi) psi, plus the forward-difference
-// gradient; the overlap gives the discrete energy of Sec. IV.C).  Order of the accumulators:
+// gradient; the overlap gives the discrete energy of Sec. IV.B).  Order of the accumulators:
 enum ObsIndex {
     OBS_NORM_QUBIT = 0,
     OBS_NORM_BOSON = 1,

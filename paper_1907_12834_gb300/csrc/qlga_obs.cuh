@@ -37,7 +37,7 @@ __device__ __forceinline__ void load_pair_abi(const T* X, int64_t nsites, int m,
     b = {p[2], p[3]};
 }
 
-// Local terms of one site from its boson field psi (Sec. IV.A): |F|^2, with F_z = psi^dagger f_z
+// Local terms of one site from its boson field psi (Sec. III.B): |F|^2, with F_z = psi^dagger f_z
 // psi and F_+ = psi^dagger f_+ psi (f_+ = f_x + i f_y, so |F|^2 = F_z^2 + |F_+|^2), and the singlet
 // pair amplitude theta = psi^T J psi = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2.
 template <class T>

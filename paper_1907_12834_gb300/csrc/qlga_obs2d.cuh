@@ -1,7 +1,7 @@
 // qlga_obs2d.cuh -- observables of a 2D FP32 lattice held pending K, in one read of the state.
 //
 // Between steps the library holds X with the true state K X (Sec. VII.B: a run is K (U K)^(n-1)
-// U, so each step is one fused pass).  The observables of Sec. IV.A (qubit and boson norms,
+// U, so each step is one fused pass).  The observables of Sec. III.B (qubit and boson norms,
 // populations, energy, singlet amplitude and fraction, overlap) need the true state; the fused
 // read-out below applies K with the warp-strip machinery of the fused step (strip_kinetic_rows)
 // and, instead of storing K X, sums the per-site terms in compensated FP32 per-lane sums.

@@ -41,7 +41,7 @@ def pin_table1(orc):
 
 
 def pin_table2(orc):
-    """max deviation from Table II (Sec. IV.A): F_par and F_perp read off V(c) at couplings
+    """max deviation from Table II (Sec. III.B): F_par and F_perp read off V(c) at couplings
     (0, 1, 0), where V = F.f, and |A00| from the oracle's singlet sum on a one-site lattice.
     Entries flagged as misprints are skipped."""
     worst = 0.0
@@ -278,7 +278,7 @@ def pin_norm(orc, ndim=2, nsteps=4):
 # ----------------------------------------------------------------- per-site fields
 
 def pin_fields(orc):
-    """Per-site fields: Table II values on uniform Thomas-Fermi lattices (Sec. IV.A), unit colour
+    """Per-site fields: Table II values on uniform Thomas-Fermi lattices (Sec. III.B), unit colour
     vectors (Eq. colormap), zero vorticity for a plane wave, the discrete curl summing to exactly
     zero over the torus, and +-2 pi around a vortex / antivortex (Sec. VI.B)."""
     from paper_1907_12834_gb300 import inputs

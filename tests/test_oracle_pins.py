@@ -29,7 +29,7 @@ def test_table1_transcriptions_agree():
 
 
 def test_table2_characteristics(orc):
-    """Sec. IV.A / Table II: |F_par|, |F_perp|, |A00| of the Table I rows."""
+    """Sec. III.B / Table II: |F_par|, |F_perp|, |A00| of the Table I rows."""
     assert pins.pin_table2(orc) < 1e-12
 
 
@@ -190,7 +190,7 @@ def test_magnetisation_exact_for_single_level_state(orc):
 
 def test_kicked_soliton_moves_at_2p_and_obeys_dispersion(orc):
     """Sec. III.C: a bright soliton kicked by e^{ipx} moves at 2p (m = 1/2) and has energy
-    E = p^2 - k^2 (Eq. dispersion), measured with the discrete energy of Sec. IV.C."""
+    E = p^2 - k^2 (Eq. dispersion), measured with the discrete energy of Sec. IV.B."""
     L, eps, nk = 1024, 0.1, 8
     j = np.arange(L)
     p_lat = 2 * np.pi * nk / L
@@ -211,8 +211,43 @@ def test_kicked_soliton_moves_at_2p_and_obeys_dispersion(orc):
     assert abs(dx - 2 * p_lat * n) < 0.01 * 2 * p_lat * n
 
 
+def _dip_centroid(st, L):
+    """Position (sites) of the two density dips of a periodic dark pair, which sit half a lattice
+    apart: the circular centroid of the density deficit at period L/2."""
+    rho = (np.abs(I.state_to_boson(st)) ** 2).sum(axis=(0, 1))
+    z = ((rho.max() - rho) * np.exp(4j * np.pi * np.arange(L) / L)).sum()
+    return (np.angle(z) % (2 * np.pi)) * L / (4 * np.pi)
+
+
+@pytest.mark.parametrize("nk", [0, 8])
+def test_dark_soliton_pair_dispersion_and_velocity(orc, nk):
+    """Dark solitons (Sec. III.C, Eq. darkdispersion): a kink c k tanh(k x) kicked by e^{ipx} has
+    E = p^2 + 2k^2 and moves at 2p.  On the periodic lattice the paper's product of two kinks
+    (Sec. IV.A, dark solitons) with L/2 = 51 physical units between them is an eigenstate up to
+    e^{-2 k L/4} tails; row 1 at E = 2 (k = 1) with the couplings (1, 0.1, 1) that make it real.
+    The energy is the discrete one of Sec. IV.B."""
+    L, eps, g = 1024, 0.1, (1.0, 0.1, 1.0)
+    j = np.arange(L)
+    p_lat = 2 * np.pi * nk / L
+    psi = I.dark_soliton_pair(eps * j, eps * L, 1, g) * np.exp(1j * p_lat * j)[None, :]
+    st = np.ascontiguousarray(I.boson_to_state(psi, eps))
+    cfg = oracle.make_cfg(1, L, 1, *g)
+    x0 = _dip_centroid(st, L)
+    orc.step(st, cfg, 20)
+    prev = st.copy()
+    orc.step(st, cfg, 1)
+    o = orc.observables(st, cfg, ref=prev)
+    E_lat = -np.angle(complex(o["overlap_re"], -o["overlap_im"]))   # -arg <psi(t-1)|psi(t)>
+    p = p_lat / eps
+    assert abs(E_lat / eps ** 2 - (p ** 2 + 2.0)) < 0.01
+    n = 100
+    orc.step(st, cfg, n - 21)
+    dx = _dip_centroid(st, L) - x0
+    assert abs(dx - 2 * p_lat * n) < 0.02 * 2 * p_lat * n + 0.05
+
+
 def test_fields(orc):
-    """Per-site F_par, F_perp, |A00|, colour map and vorticity (Sec. IV.A, VI.B)."""
+    """Per-site F_par, F_perp, |A00|, colour map and vorticity (Sec. III.B, VI.B)."""
     assert pins.pin_fields(orc) < 1e-12
 
 

@@ -203,8 +203,8 @@ def alu_roofline(sites, kernel_ms, sms):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FMA-pipe issue cycles/s",
             "frac": achieved / peak, "cycles_per_site": per_site,
             "peak_source": "4 sub-partitions x %d SMs x %s" % (sms, src),
-            "note": "FP32 FMA-pipe issue cycles per site from ncu on the settled 2048^2 state "
-                    "(profiles/step2d_f32_2048_full.md); the pipe, not HBM, bounds the fused step"}
+            "note": "FP32 FMA-pipe issue cycles per site from an ncu --set full capture of the fused "
+                    "step on the settled 2048^2 state; the pipe, not HBM, bounds the fused step"}
 
 
 def recorded_traffic(n):
@@ -343,7 +343,7 @@ def run_gb300(args):
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
                      "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
                      "note": "the fused step is limited by FP32 FMA-pipe cycles of the potential "
-                             "(ncu on the settled state: %s; profiles/step2d_f32_2048_full.md), "
+                             "(ncu --set full on the settled 2048^2 state: %s), "
                              "not by HBM traffic" % counters_note()},
         "alu": alu_roofline(sites, kernel_ms, torch.cuda.get_device_properties(0).multi_processor_count),
         "e2e": e2e,
@@ -501,10 +501,160 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     out["note"] = ("rates on the device with CUDA events (adjoint: wall time of the two calls, host "
                    "synchronised); gradient_site_steps_per_s counts sites x steps of a full gradient "
                    "(forward with checkpoints + recompute + pull-back); norm_identity_error = "
-                   "|dL/dx0 - x0| / |x0| for L = |x_n|^2 / 2")
+                   "|dL/dx0 - x0| / |x0| for L = |x_n|^2 / 2; 'accuracy' of a path: its kernels run "
+                   "on a short case of the path's recipe against the FP64 oracle's stored results")
+    acc = path_accuracy(torch, qlga, inputs) or {}
+    lh = long_horizon_record(torch, qlga, inputs)
+    for key, src in (("config0_fp64_1d", "config0_fp64_1d"), ("interleaved_fp32_2d", "interleaved_fp32_2d"),
+                     ("batched_fp32_1d", "batched_fp32_1d"), ("batched_fp32_2d", "batched_fp32_2d"),
+                     ("adjoint_fp32_2d_512", "adjoint_fp32_2d"), ("adjoint_fp64_2d_512", "adjoint_fp64_2d")):
+        if src in acc and key in out:
+            out[key]["accuracy"] = acc[src]
+    for key, prec, name in (("config1_fp32_1d", 32, "config1_g_integrable_set"),
+                            ("config1_fp64_1d", 64, "config1_g_integrable_set"),
+                            ("plain_fp64_2d", 64, "config2_512")):
+        if name in lh and key in out:
+            r = lh[name]
+            out[key]["accuracy"] = {"workload": name, "steps": r["steps"][-1],
+                                    "rel_l2_vs_oracle": r["gpu_fp%d_vs_oracle" % prec][-1],
+                                    "oracle_perturbed_1e-13": r["oracle_perturbed_1e-13"][-1],
+                                    "norm_drift": r["gpu_fp%d_norm_drift" % prec]}
+    out["long_horizon"] = lh
     return out
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _rel(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _sample(state, sites):
+    """The state (library layout) at flat site indices: (5, len(sites), 2, 2)."""
+    return state.reshape(5, -1, 2, 2)[:, sites]
+
+
+def long_horizon_record(torch, qlga, inputs, names=None):
+    """GPU FP64 and FP32 runs of the long-horizon workloads against the FP64 oracle's stored
+    trajectory (tests/golden/long_horizon_*.npz, written by a script that calls only the oracle),
+    every checkpoint: relative L2 at the stored sample of sites; beside them the growth of a
+    1e-13 relative perturbation of the initial state, in the oracle (stored) and in the GPU FP64
+    run (full lattice), which shows how far the dynamics itself amplifies rounding."""
+    import numpy as np
+    out = {}
+    for name in names or inputs.LONG_HORIZON:
+        path = os.path.join(GOLDEN, "long_horizon_%s.npz" % name)
+        if not os.path.exists(path):
+            continue
+        G = np.load(path)
+        ndim, nx, ny, g, steps, every, x0 = inputs.long_horizon_workload(name)
+        rec = {"lattice": [nx, ny] if ndim == 2 else nx, "couplings": list(g),
+               "steps": [int(k) for k in G["steps"]], "oracle_perturbed_1e-13": [float(v) for v in G["oracle_growth"]]}
+        for prec in (64, 32):
+            dt = np.float64 if prec == 64 else np.float32
+            lat = qlga.Lattice(ndim, nx, ny, precision=prec, g=g)
+            lat.load_state(x0.astype(dt))
+            latp = None
+            if prec == 64:
+                latp = qlga.Lattice(ndim, nx, ny, precision=prec, g=g)
+                latp.load_state(inputs.perturbed(x0))
+            errs, growth, norm = [], [], []
+            for k, step in enumerate(G["steps"]):
+                if step > 0:
+                    lat.step(every)
+                    if latp is not None:
+                        latp.step(every)
+                st = lat.get_state()
+                errs.append(_rel(_sample(st, G["sites"][k]), G["samples"][k]))
+                norm.append(float((st.astype(np.float64) ** 2).sum()))
+                if latp is not None:
+                    growth.append(_rel(latp.get_state(), st))
+            lat.close()
+            if latp is not None:
+                latp.close()
+                rec["gpu_fp64_perturbed_1e-13"] = growth
+            rec["gpu_fp%d_vs_oracle" % prec] = errs
+            rec["gpu_fp%d_norm_drift" % prec] = abs(norm[-1] - norm[0]) / norm[0]
+        out[name] = rec
+    return out
+
+
+def path_accuracy(torch, qlga, inputs):
+    """Each timed path run on a short case of its own recipe and compared with the FP64 oracle's
+    stored results (tests/golden/path_accuracy.npz): relative L2 at the stored sites (whole state
+    for config 0), with the qubit-norm drift of the run."""
+    import numpy as np
+    path = os.path.join(GOLDEN, "path_accuracy.npz")
+    if not os.path.exists(path):
+        return None
+    G = np.load(path)
+    W = inputs.path_accuracy_workloads()
+    out = {}
+
+    def lattice_run(w, prec, steps, interleave=0):
+        lat = qlga.Lattice(w.ndim, w.nx, w.ny, precision=prec, g=w.g, interleave=interleave)
+        lat.load_state(w.state.astype(np.float32 if prec == 32 else np.float64))
+        n0 = lat.observables()["norm_qubit"]
+        lat.step(steps)
+        o = lat.observables()
+        st = lat.get_state()
+        lat.close()
+        return st, abs(o["norm_qubit"] - n0) / n0
+
+    c = W["config0"]
+    st, dn = lattice_run(c["w"], 64, c["steps"])
+    out["config0_fp64_1d"] = {"steps": c["steps"], "rel_l2_vs_oracle": _rel(st, G["config0_state"]),
+                              "norm_drift": dn}
+    c = W["interleaved"]
+    st, dn = lattice_run(c["w"], 32, c["steps"], interleave=1)
+    out["interleaved_fp32_2d"] = {"lattice": [c["w"].nx, c["w"].ny], "steps": c["steps"],
+                                  "rel_l2_vs_oracle": _rel(_sample(st, G["interleaved_sites"]),
+                                                           G["interleaved_samples"]), "norm_drift": dn}
+    for key, heights_of in (("batch1d", None), ("batch2d", "heights")):
+        c = W[key]
+        b = c["w"]
+        hs = b.meta["heights"] if heights_of else np.ones(len(b.lengths), dtype=np.int64)
+        kw = {"heights": hs} if heights_of else {}
+        bt = qlga.Batch(b.lengths, b.couplings, precision=32, **kw)
+        bt.load_state(b.state.astype(np.float32))
+        bt.step(c["steps"])
+        got = bt.get_state().astype(np.float64)
+        bt.close()
+        sizes = b.lengths * hs
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        sites = G[key + "_sites"]
+        run = np.searchsorted(offs, sites, side="right") - 1
+        gs = np.empty((5, len(sites), 2, 2))
+        for r in np.unique(run):
+            sel = run == r
+            part = got[20 * offs[r]:20 * (offs[r] + sizes[r])].reshape(5, -1, 2, 2)
+            gs[:, sel] = part[:, sites[sel] - offs[r]]
+        n0 = float((b.state.astype(np.float64) ** 2).sum())
+        out["batched_fp32_%s" % key[-2:]] = {"runs": int(len(b.lengths)), "steps": c["steps"],
+                                            "rel_l2_vs_oracle": _rel(gs, G[key + "_samples"]),
+                                            "norm_drift": abs(float((got ** 2).sum()) - n0) / n0}
+    c = W["adjoint"]
+    w4 = c["w"]
+    for prec in (32, 64):
+        dt = torch.float32 if prec == 32 else torch.float64
+        x0 = torch.tensor(w4.state, dtype=dt, device="cuda")
+        cot_in = torch.tensor(inputs.adjoint_cotangent(w4.state.shape, c["cotangent_seed"]), dtype=dt, device="cuda")
+        with qlga.Lattice(2, w4.nx, w4.ny, precision=prec, g=w4.g) as lat:
+            cot, dg = lat.gradient(x0, c["steps"], cot_in, checkpoint_every=30)
+        cn = cot.double().cpu().numpy()
+        out["adjoint_fp%d_2d" % prec] = {
+            "lattice": [w4.nx, w4.ny], "steps": c["steps"],
+            "rel_l2_vs_oracle": _rel(_sample(cn, G["adjoint_sites"]), G["adjoint_cot_samples"]),
+            "coupling_gradient_rel_vs_oracle": float(np.abs(np.asarray(dg) - G["adjoint_dg"]).max() /
+                                                     np.abs(G["adjoint_dg"]).max())}
+    return out
+
+
+E2E_REPEATS = 3
 E2E_REPEATS = 3
 
 

@@ -146,6 +146,69 @@ qlga_status qlga_apply_kinetic(qlga_handle* h);
  * <psi(t) | psi_ref> of the boson fields is filled in (the discrete energy of Sec. IV.B). */
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out);
 
+/* ---------------------------------------------------------------------------------------
+ * Slab decomposition (Sec. VII.C, "Speed, size and scalability": the lattice is split over
+ * several GPUs).  A 2D lattice of nx x ny sites is cut along y into slabs; each slab is an
+ * ordinary handle whose lattice holds the slab's rows plus a halo of H >= 5 rows on each side
+ * (its own periodic wrap in y only ever touches the halo).  One step moves a site's
+ * dependency cone at most 4 rows along y (the four kinetic blocks of the axis), so if the halo
+ * rows hold the neighbouring slabs' rows before every qlga_step(h, 1), the slab's own rows come
+ * out exactly as in the whole lattice; halo rows hold stale values after a step until the next
+ * exchange.  The fifth halo row serves the forward difference of the energy at the slab's last
+ * row.  A read-out (qlga_get_state, qlga_observable_sums) also needs fresh halo rows.
+ * --------------------------------------------------------------------------------------- */
+enum { QLGA_ROWS_OUT = 0, QLGA_ROWS_IN = 1 };
+
+/* Copy rows [y0, y0 + nrows) of all 5 planes of the handle's current state buffer, as held
+ * (the library's own representation, opaque to the caller), to (QLGA_ROWS_OUT) or from
+ * (QLGA_ROWS_IN) `buf`: device memory of 5 * nrows * nx * 16 bytes (FP32) or 32 (FP64), laid
+ * out [plane][row][x], owned by the caller.  Enqueued on the handle's stream (one
+ * cudaMemcpy2DAsync).  The rows move between handles of the same nx and precision that have
+ * taken the same steps, e.g. through NCCL send / recv between ranks.  INVALID_ARG for rows
+ * outside the lattice or a bad direction. */
+qlga_status qlga_copy_rows(qlga_handle* h, int64_t y0, int64_t nrows, void* buf, int direction);
+
+/* Copy rows [ysrc, ysrc + nrows) of src's current state buffer into rows [ydst, ...) of
+ * dst's: two handles of the same nx, precision and dimension that have taken the same steps,
+ * on one device or on two devices with peer access.  The copy runs on dst's stream after the
+ * work queued on src's stream, and src's stream waits for it.  INVALID_ARG for mismatched
+ * handles, rows outside a lattice or overlapping rows of one handle. */
+qlga_status qlga_exchange_rows(qlga_handle* src, int64_t ysrc, qlga_handle* dst, int64_t ydst,
+                               int64_t nrows);
+
+/* The 14 FP64 sums behind qlga_obs over the rows [y0, y1) of the current true state (the
+ * forward difference of row y1 - 1 reads row y1, or row 0 when y1 == ny), written to sums[14]
+ * (host memory): qubit norm, boson norm, the 5 populations, energy, singlet amplitude (re,
+ * im), sum |psi^T J psi|^2, sum rho^2 and the overlap with `ref_state_device` (re, im; 0 when
+ * it is NULL).  Sums of disjoint row ranges add up (an all-reduce over slabs); waits for the
+ * stream.  Sec. III.B Eq. cmap, Sec. IV.B Eq. disecrete_energy. */
+qlga_status qlga_observable_sums(qlga_handle* h, int64_t y0, int64_t y1, const void* ref_state_device,
+                                 double* sums);
+
+/* qlga_obs from the 14 sums of qlga_observable_sums (host only): magnetisation and singlet
+ * fraction are formed from the sums.  NOT_FINITE when the norm or the energy is not finite. */
+qlga_status qlga_obs_from_sums(const double* sums, int64_t step, qlga_obs* out);
+
+/* Objectives of a state that gradients are taken of, with their cotangent (Sec. III.B Eq. cmap:
+ * the populations and the singlet pair amplitude psi^T J psi; the energy is the functional
+ * whose variation is the right-hand side of Eq. eomspin2, forward differences for the
+ * gradient term, as in qlga_obs):
+ *   values[0] = P = sum |a_l|^2 + |b_l|^2 of level `level` (0..4 for m = +2..-2),
+ *   values[1] = S = sum |psi^T J psi|^2 / sum rho^2 (the singlet fraction),
+ *   values[2] = E = sum_sites [sum_axis sum_m |psi_m(j+1) - psi_m(j)|^2 + g0/2 rho^2
+ *                              + g1/2 |F|^2 + g2/10 |psi^T J psi|^2]   with the couplings g[3].
+ * `x_device` is a state of the handle's shape and precision in the layout above (device
+ * memory, caller-owned, not the handle's own buffers).  With `cot_device` (same shape, layout
+ * and precision, device memory) the call also writes the cotangent of L = weights[0] P +
+ * weights[1] S + weights[2] E: dL/d(each real of the state), i.e. dL/dRe z + i dL/dIm z per
+ * amplitude; with `dg` (3 host doubles) it writes L's own dependence on the couplings, dL/dg0 =
+ * weights[2] sum rho^2 / 2, dL/dg1 = weights[2] sum |F|^2 / 2, dL/dg2 = weights[2] sum
+ * |psi^T J psi|^2 / 10.  Sums in FP64 (compensated per thread for FP32 states); uses the
+ * handle's work memory and stream and waits for it.  INVALID_ARG for a bad level, missing
+ * weights, or non-finite couplings; NOT_FINITE for a state holding NaN or Inf. */
+qlga_status qlga_objective(qlga_handle* h, const void* x_device, int32_t level, const double* g,
+                           const double* weights, double* values, double* dg, void* cot_device);
+
 /* Per-site diagnostic fields of the current state (Sec. III.B Eq. cmap and Eq. colormap,
  * Sec. VI.B Eqs. velocity / pointwise_vorticity), written to `dst` as 11 planes of ny*nx
  * values in the handle's precision, x fastest:
@@ -171,17 +234,18 @@ qlga_status qlga_fields(qlga_handle* h, void* dst, int where);
  *
  * Scratch: the block partial sums live in one file-scope __device__ array of 1216 partial rows
  * of 14 doubles plus the 14 results (136,304 bytes), which every GPU that loads the library
- * holds until the process exits.  The reduction grid is capped at those 1216 rows, so every
- * configuration that qlga_state_bytes() accepts fits; a configuration it rejects, or a grid that
- * would need more rows, is rejected with QLGA_ERR_INVALID_ARG.  Nothing is allocated: no
+ * holds until the process exits.  The reduction is a grid-stride loop over at most 1216 blocks,
+ * one partial row each, so every configuration that qlga_state_bytes() accepts fits; a
+ * configuration it rejects is rejected here with QLGA_ERR_INVALID_ARG.  Nothing is allocated: no
  * cudaMalloc, cudaFree or allocating library routine is called.
  *
- * Set-up: the first call on each device (with that device current) looks up the device
- * address of the scratch array with cudaGetSymbolAddress; make that first call before any
- * stream capture.  All calls on a device share the one array, which keeps the last call's
- * contents; each call overwrites every partial row it reads, so nothing needs clearing, but
- * calls whose work overlaps on the GPU (different streams or host threads) race on the array
- * and must be serialised by the caller. */
+ * Each call, on the current device, looks up the device address of the array with
+ * cudaGetSymbolAddress (it allocates nothing, and a fresh lookup stays valid after a
+ * cudaDeviceReset), launches the reduction on `stream`, copies the 14 results to `out` and waits
+ * for `stream` to finish.  All calls on a device share the one array, which keeps the last
+ * call's contents; each call overwrites every partial row it reads, so nothing needs clearing,
+ * but calls whose work overlaps on the GPU (different streams or host threads) race on the
+ * array and must be serialised by the caller. */
 qlga_status qlga_observables_noalloc(const qlga_config* cfg, const void* state_device,
                                      const void* ref_state_device, void* stream, qlga_obs* out);
 

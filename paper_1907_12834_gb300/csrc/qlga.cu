@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,6 +36,7 @@
 #include "qlga_interleave.cuh"
 #include "qlga_step2d_f64.cuh"
 #include "qlga_obs2d.cuh"
+#include "qlga_objective.cuh"
 
 #include <vector>
 
@@ -43,7 +45,9 @@ using namespace qlga;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kObsMaxBlocks = 152 * 8;
+// Capacity (rows of block partials) of the observables reduction: 8 blocks per SM on a 152-SM
+// GB300.  Grids take min(capacity, 8 x the device's SM count) blocks; the loops are grid-stride.
+constexpr int kObsMaxBlocks = 1216;
 constexpr int64_t kGraphMaxSites = int64_t(1) << 18;  // lattices replayed from step graphs
 constexpr int kGraphDefaultSteps = 32;
 
@@ -70,6 +74,26 @@ qlga_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// SM count of the current device, queried once per device (152 on GB300; the fallback only
+// applies if the query itself fails, and then the next launch reports the error).
+int device_sms() {
+    constexpr int kMax = 64;
+    static std::atomic<int> cache[kMax];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 152;
+    if (dev < kMax) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 152;
+    if (dev < kMax) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
+// Blocks of the grid-stride observables reduction on the current device.
+int obs_blocks_cap() { return std::min(kObsMaxBlocks, 8 * device_sms()); }
 
 }  // namespace
 
@@ -183,19 +207,21 @@ __global__ void k_load_boson(const T* __restrict__ psi5, T* __restrict__ X, int6
 }
 
 // Per-site observable terms in the state's precision, block sums (FP64) into
-// partials[block][OBS_COUNT].  X_RESIDENT: X is in the resident layout (else the ABI layout);
-// the reference state is always a caller buffer in the ABI layout.
+// partials[block][OBS_COUNT], over the sites [s0, s1) (rows of whole sites: the forward pairs
+// wrap periodically only at the lattice's own edge).  X_RESIDENT: X is in the resident layout
+// (else the ABI layout); the reference state is always a caller buffer in the ABI layout.
 template <class T, bool RESIDENT>
 __global__ void __launch_bounds__(kThreads) k_observables(const T* __restrict__ X,
                                                           const T* __restrict__ ref, int64_t nx,
                                                           int64_t ny, int ndim, double g0,
                                                           double g1, double g2,
-                                                          double* __restrict__ partials) {
+                                                          double* __restrict__ partials,
+                                                          int64_t s0, int64_t s1) {
     const int64_t nsites = nx * ny;
     ThreadSum<T> acc[OBS_COUNT];
     const T hg0 = T(0.5 * g0), hg1 = T(0.5 * g1), tg2 = T(0.1 * g2);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t site = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < nsites; site += stride) {
+    for (int64_t site = s0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; site < s1; site += stride) {
         const int64_t x = site % nx, y = site / nx;
         cpx<T> psi[5];
         T rho = T(0);
@@ -594,7 +620,8 @@ inline int step2d_f32_launch(const float* in, float* out, int64_t nx, int64_t ny
 // size (at most ~6 bytes per site beside the 80-byte state).
 inline int obs2d_edge_blocks(int64_t strips, int64_t ny) {
     const int64_t b = (strips * ny + kObs2dEdgeThreads - 1) / kObs2dEdgeThreads;
-    return int(b < 1 ? 1 : (b > kObs2dEdgeBlocksMax ? kObs2dEdgeBlocksMax : b));
+    const int64_t cap = std::min<int64_t>(kObs2dEdgeBlocksMax, 4 * int64_t(device_sms()));
+    return int(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 inline size_t obs2d_edge_bytes(int64_t nx, int64_t ny) {
@@ -798,20 +825,25 @@ qlga_status check_cfg(const qlga_config* c) {
 }
 
 // Threads per block for the per-site kernels: 256, or fewer for small lattices so that the grid
-// still spreads over every SM (2 x 152 blocks), never below one warp.
+// still spreads over every SM (2 blocks per SM), never below one warp.
 int block_for(int64_t n) {
-    int64_t t = (n + 2 * 152 - 1) / (2 * 152);
+    const int64_t b = 2 * int64_t(device_sms());
+    int64_t t = (n + b - 1) / b;
     t = (t + 31) / 32 * 32;
     return int(t < 32 ? 32 : (t > kThreads ? kThreads : t));
 }
 
-int grid_for_block(int64_t n, int threads, int cap = 152 * 16) {
+// Grid of a grid-stride per-site kernel: one block per `threads` sites, at most `cap` blocks
+// (cap = 0: 16 per SM of the current device).
+int grid_for_block(int64_t n, int threads, int cap = 0) {
+    if (cap <= 0) cap = 16 * device_sms();
     int64_t g = (n + threads - 1) / threads;
     if (g > cap) g = cap;
     return int(g < 1 ? 1 : g);
 }
 
-int grid_for(int64_t n, int cap = 152 * 16) {
+int grid_for(int64_t n, int cap = 0) {
+    if (cap <= 0) cap = 16 * device_sms();
     int64_t g = (n + kThreads - 1) / kThreads;
     if (g > cap) g = cap;
     return int(g < 1 ? 1 : g);
@@ -864,11 +896,12 @@ void interleave_launch_t(qlga_handle* h, const void* in, void* out, int axis) {
     const int64_t nx = h->cfg.nx, ny = h->cfg.ny;
     if (axis == 0) {
         const int64_t tiles = ((nx + kIlvXTile - 1) / kIlvXTile) * ny;
-        const int grid = int(tiles < 152 * 16 ? tiles : 152 * 16);
+        const int64_t cap = 16 * int64_t(device_sms());
+        const int grid = int(tiles < cap ? tiles : cap);
         k_interleave_x<T, V><<<grid, kIlvXThreads, 0, h->stream>>>(static_cast<const T*>(in), static_cast<T*>(out), nx, ny, PC, h->status);
     } else {
         const int64_t strips = (nx + kIlvYThreads - 1) / kIlvYThreads;
-        int64_t chunks = (152 * 8) / strips;
+        int64_t chunks = (8 * int64_t(device_sms())) / strips;
         chunks = chunks < 1 ? 1 : (chunks > ny ? ny : chunks);
         k_interleave_y<T, V><<<int(strips * chunks), kIlvYThreads, 0, h->stream>>>(static_cast<const T*>(in), static_cast<T*>(out), nx, ny, int(chunks), PC, h->status);
     }
@@ -1229,36 +1262,24 @@ qlga_status graph_steps_launch(qlga_handle* h) {
 //
 // Scratch of qlga_observables_noalloc(): kNoAllocRows block partials of OBS_COUNT doubles, then
 // the OBS_COUNT results.  Host code must not pass the array's name to a kernel (in host code it
-// names a host-side stand-in); the device address comes from cudaGetSymbolAddress, looked up
-// once per device and cached.
+// names a host-side stand-in); the device address comes from cudaGetSymbolAddress, looked up on
+// every call, so it stays valid after the caller resets the device and the module is reloaded.
 
 namespace {
 constexpr int kNoAllocRows = kObsMaxBlocks;
 constexpr size_t kNoAllocDoubles = size_t(kNoAllocRows) * OBS_COUNT + OBS_COUNT;
-constexpr int kNoAllocMaxDevices = 64;
 }  // namespace
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 namespace {
 
-std::mutex g_noalloc_mutex;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up on first use).
+// Device address of the scratch array on the current device.
 qlga_status noalloc_scratch(double** addr) {
-    int dev = 0;
-    QLGA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices)
-        return fail(QLGA_ERR_UNSUPPORTED, "device ordinal beyond the scratch address table%s");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(observables scratch)");
-        g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
-    *addr = g_noalloc_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(observables scratch)");
+    *addr = static_cast<double*>(p);
     return QLGA_OK;
 }
 
@@ -1271,9 +1292,8 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
     if (s != QLGA_OK) return s;
     if (!state_device || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
     const int64_t n = nsites_of(*cfg);
-    const int blocks = grid_for(n, kNoAllocRows);
-    if (blocks > kNoAllocRows)
-        return fail(QLGA_ERR_INVALID_ARG, "reduction needs more partial rows than the static scratch holds%s");
+    // grid-stride reduction: at most kNoAllocRows blocks, one partial row each, whatever the size
+    const int blocks = grid_for(n, std::min(kNoAllocRows, 8 * device_sms()));
     double* scratch = nullptr;
     s = noalloc_scratch(&scratch);
     if (s != QLGA_OK) return s;
@@ -1283,12 +1303,12 @@ extern "C" qlga_status qlga_observables_noalloc(const qlga_config* cfg, const vo
         k_observables<float, false><<<blocks, kThreads, 0, st>>>(static_cast<const float*>(state_device),
                                                           static_cast<const float*>(ref_state_device),
                                                           cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
-                                                          cfg->g2, scratch);
+                                                          cfg->g2, scratch, 0, n);
     else
         k_observables<double, false><<<blocks, kThreads, 0, st>>>(static_cast<const double*>(state_device),
                                                            static_cast<const double*>(ref_state_device),
                                                            cfg->nx, cfg->ny, cfg->ndim, cfg->g0, cfg->g1,
-                                                           cfg->g2, scratch);
+                                                           cfg->g2, scratch, 0, n);
     QLGA_CUDA(cudaGetLastError(), "k_observables launch (no-alloc)");
     k_reduce_partials<<<OBS_COUNT, kReduceThreads, 0, st>>>(scratch, blocks, OBS_COUNT, result);
     QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch (no-alloc)");
@@ -1536,6 +1556,48 @@ qlga_status qlga_apply_kinetic(qlga_handle* h) {
     return QLGA_OK;
 }
 
+// Partial rows of the observable sums of the handle's true state over the rows [y0, y1) (the
+// forward pair of row y1 - 1 reads row y1, or row 0 when y1 == ny), with the optional
+// reference state for the overlap: *partials, *rows.
+static qlga_status observables_rows_partials(qlga_handle* h, const void* ref_state_device, int64_t y0, int64_t y1,
+                                      double** partials, int* rows) {
+    const void* view = nullptr;
+    qlga_status s = true_state_view(h, &view);
+    if (s != QLGA_OK) return s;
+    const int64_t s0 = y0 * h->cfg.nx, s1 = y1 * h->cfg.nx;
+    const int blocks = grid_for(s1 - s0, obs_blocks_cap());
+    if (h->cfg.precision == 32)
+        k_observables<float, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
+                                                                 h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials, s0, s1);
+    else
+        k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
+                                                                  h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials, s0, s1);
+    QLGA_CUDA(cudaGetLastError(), "k_observables launch");
+    h->launches += 1;
+    *partials = h->partials;
+    *rows = blocks;
+    return QLGA_OK;
+}
+
+// The observables of qlga_obs from the OBS_COUNT sums.
+static void fill_obs(const double* o, int64_t step, qlga_obs* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->norm_qubit = o[OBS_NORM_QUBIT];
+    out->norm_boson = o[OBS_NORM_BOSON];
+    out->magnetisation = 0.0;
+    for (int m = 0; m < 5; ++m) {
+        out->pop[m] = o[OBS_POP0 + m];
+        out->magnetisation += double(2 - m) * o[OBS_POP0 + m];
+    }
+    out->energy = o[OBS_ENERGY];
+    out->singlet_re = o[OBS_SINGLET_RE];
+    out->singlet_im = o[OBS_SINGLET_IM];
+    out->singlet_fraction = o[OBS_RHO2] > 0 ? o[OBS_THETA2] / o[OBS_RHO2] : 0.0;
+    out->overlap_re = o[OBS_OVERLAP_RE];
+    out->overlap_im = o[OBS_OVERLAP_IM];
+    out->step = step;
+}
+
 // Partial rows of the observable sums of the handle's true state (with the optional reference
 // state for the overlap): *partials, *rows.
 qlga_status observables_partials(qlga_handle* h, const void* ref_state_device, double** partials, int* rows) {
@@ -1552,21 +1614,7 @@ qlga_status observables_partials(qlga_handle* h, const void* ref_state_device, d
             return QLGA_OK;
         }
     }
-    const void* view = nullptr;
-    qlga_status s = true_state_view(h, &view);
-    if (s != QLGA_OK) return s;
-    const int blocks = grid_for(nsites_of(h->cfg), kObsMaxBlocks);
-    if (h->cfg.precision == 32)
-        k_observables<float, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const float*>(view), static_cast<const float*>(ref_state_device),
-                                                                 h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
-    else
-        k_observables<double, true><<<blocks, kThreads, 0, h->stream>>>(static_cast<const double*>(view), static_cast<const double*>(ref_state_device),
-                                                                  h->cfg.nx, h->cfg.ny, h->cfg.ndim, h->cfg.g0, h->cfg.g1, h->cfg.g2, h->partials);
-    QLGA_CUDA(cudaGetLastError(), "k_observables launch");
-    h->launches += 1;
-    *partials = h->partials;
-    *rows = blocks;
-    return QLGA_OK;
+    return observables_rows_partials(h, ref_state_device, 0, h->cfg.ny, partials, rows);
 }
 
 qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_obs* out) {
@@ -1581,25 +1629,139 @@ qlga_status qlga_observables(qlga_handle* h, const void* ref_state_device, qlga_
     double o[OBS_COUNT];
     QLGA_CUDA(cudaMemcpyAsync(o, h->obs_dev, sizeof(o), cudaMemcpyDeviceToHost, h->stream), "observables copy");
     QLGA_CUDA(cudaStreamSynchronize(h->stream), "observables sync");
-    std::memset(out, 0, sizeof(*out));
-    out->norm_qubit = o[OBS_NORM_QUBIT];
-    out->norm_boson = o[OBS_NORM_BOSON];
-    out->magnetisation = 0.0;
-    for (int m = 0; m < 5; ++m) {
-        out->pop[m] = o[OBS_POP0 + m];
-        out->magnetisation += double(2 - m) * o[OBS_POP0 + m];
-    }
-    out->energy = o[OBS_ENERGY];
-    out->singlet_re = o[OBS_SINGLET_RE];
-    out->singlet_im = o[OBS_SINGLET_IM];
-    out->singlet_fraction = o[OBS_RHO2] > 0 ? o[OBS_THETA2] / o[OBS_RHO2] : 0.0;
-    out->overlap_re = o[OBS_OVERLAP_RE];
-    out->overlap_im = o[OBS_OVERLAP_IM];
-    out->step = h->step;
+    fill_obs(o, h->step, out);
     s = check_status_word(h);
     if (s != QLGA_OK) return s;
     if (!std::isfinite(out->norm_qubit) || !std::isfinite(out->energy))
         return fail(QLGA_ERR_NOT_FINITE, "the state holds NaN or Inf%s");
+    return QLGA_OK;
+}
+
+qlga_status qlga_observable_sums(qlga_handle* h, int64_t y0, int64_t y1, const void* ref_state_device,
+                                 double* sums) {
+    if (!h || !sums) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (y0 < 0 || y1 <= y0 || y1 > h->cfg.ny) return fail(QLGA_ERR_INVALID_ARG, "rows must satisfy 0 <= y0 < y1 <= ny%s");
+    double* partials = nullptr;
+    int rows = 0;
+    qlga_status s = observables_rows_partials(h, ref_state_device, y0, y1, &partials, &rows);
+    if (s != QLGA_OK) return s;
+    k_reduce_partials<<<OBS_COUNT, kReduceThreads, 0, h->stream>>>(partials, rows, OBS_COUNT, h->obs_dev);
+    QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
+    h->launches += 1;
+    QLGA_CUDA(cudaMemcpyAsync(sums, h->obs_dev, sizeof(double) * OBS_COUNT, cudaMemcpyDeviceToHost, h->stream),
+              "observable sums copy");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "observable sums sync");
+    return check_status_word(h);
+}
+
+qlga_status qlga_obs_from_sums(const double* sums, int64_t step, qlga_obs* out) {
+    if (!sums || !out) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    fill_obs(sums, step, out);
+    if (!std::isfinite(out->norm_qubit) || !std::isfinite(out->energy))
+        return fail(QLGA_ERR_NOT_FINITE, "the sums hold NaN or Inf%s");
+    return QLGA_OK;
+}
+
+qlga_status qlga_objective(qlga_handle* h, const void* x_device, int32_t level, const double* g,
+                           const double* weights, double* values, double* dg, void* cot_device) {
+    if (!h || !x_device || !g || !values) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (level < 0 || level > 4) return fail(QLGA_ERR_INVALID_ARG, "level must be 0..4 (m = +2..-2)%s");
+    if ((cot_device || dg) && !weights) return fail(QLGA_ERR_INVALID_ARG, "a cotangent needs the weights%s");
+    if (!std::isfinite(g[0]) || !std::isfinite(g[1]) || !std::isfinite(g[2]))
+        return fail(QLGA_ERR_INVALID_ARG, "couplings must be finite%s");
+    const int64_t n = nsites_of(h->cfg);
+    const int blocks = grid_for(n, obs_blocks_cap());  // partial rows of OBJ_COUNT <= OBS_COUNT doubles
+    const bool f = h->cfg.precision == 32;
+    if (f)
+        k_objective_sums<float><<<blocks, kObjThreads, 0, h->stream>>>(static_cast<const float*>(x_device), h->cfg.nx, h->cfg.ny,
+                                                                   h->cfg.ndim, level, g[0], g[1], g[2], h->partials);
+    else
+        k_objective_sums<double><<<blocks, kObjThreads, 0, h->stream>>>(static_cast<const double*>(x_device), h->cfg.nx, h->cfg.ny,
+                                                                    h->cfg.ndim, level, g[0], g[1], g[2], h->partials);
+    QLGA_CUDA(cudaGetLastError(), "k_objective_sums launch");
+    k_reduce_partials<<<OBJ_COUNT, kReduceThreads, 0, h->stream>>>(h->partials, blocks, OBJ_COUNT, h->obs_dev);
+    QLGA_CUDA(cudaGetLastError(), "k_reduce_partials launch");
+    h->launches += 2;
+    if (cot_device) {
+        if (f)
+            k_objective_cot<float><<<grid_for(n), kObjThreads, 0, h->stream>>>(
+                static_cast<const float*>(x_device), static_cast<float*>(cot_device), h->cfg.nx, h->cfg.ny, h->cfg.ndim,
+                level, g[0], g[1], g[2], h->obs_dev, weights[0], weights[1], weights[2]);
+        else
+            k_objective_cot<double><<<grid_for(n), kObjThreads, 0, h->stream>>>(
+                static_cast<const double*>(x_device), static_cast<double*>(cot_device), h->cfg.nx, h->cfg.ny, h->cfg.ndim,
+                level, g[0], g[1], g[2], h->obs_dev, weights[0], weights[1], weights[2]);
+        QLGA_CUDA(cudaGetLastError(), "k_objective_cot launch");
+        h->launches += 1;
+    }
+    double o[OBJ_COUNT];
+    QLGA_CUDA(cudaMemcpyAsync(o, h->obs_dev, sizeof(o), cudaMemcpyDeviceToHost, h->stream), "objective sums copy");
+    QLGA_CUDA(cudaStreamSynchronize(h->stream), "objective sync");
+    values[0] = o[OBJ_POP];
+    values[1] = o[OBJ_RHO2] > 0.0 ? o[OBJ_THETA2] / o[OBJ_RHO2] : 0.0;
+    values[2] = o[OBJ_ENERGY];
+    if (dg) {  // the energy term's explicit dependence on the couplings
+        dg[0] = weights[2] * 0.5 * o[OBJ_RHO2];
+        dg[1] = weights[2] * 0.5 * o[OBJ_F2];
+        dg[2] = weights[2] * 0.1 * o[OBJ_THETA2];
+    }
+    if (!std::isfinite(values[0]) || !std::isfinite(values[2]))
+        return fail(QLGA_ERR_NOT_FINITE, "the state holds NaN or Inf%s");
+    return QLGA_OK;
+}
+
+static size_t site_bytes_of(const qlga_config& c) { return size_t(c.precision == 32 ? 16 : 32); }
+
+qlga_status qlga_copy_rows(qlga_handle* h, int64_t y0, int64_t nrows, void* buf, int direction) {
+    if (!h || !buf) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (direction != QLGA_ROWS_OUT && direction != QLGA_ROWS_IN)
+        return fail(QLGA_ERR_INVALID_ARG, "direction must be QLGA_ROWS_OUT or QLGA_ROWS_IN%s");
+    if (y0 < 0 || nrows <= 0 || y0 + nrows > h->cfg.ny)
+        return fail(QLGA_ERR_INVALID_ARG, "rows must satisfy 0 <= y0 and y0 + nrows <= ny%s");
+    const size_t sb = site_bytes_of(h->cfg);
+    const size_t plane = size_t(nsites_of(h->cfg)) * sb;
+    const size_t width = size_t(nrows) * size_t(h->cfg.nx) * sb;
+    char* state = static_cast<char*>(h->X[h->cur]) + size_t(y0) * size_t(h->cfg.nx) * sb;
+    if (direction == QLGA_ROWS_OUT)
+        QLGA_CUDA(cudaMemcpy2DAsync(buf, width, state, plane, width, 5, cudaMemcpyDefault, h->stream), "qlga_copy_rows out");
+    else
+        QLGA_CUDA(cudaMemcpy2DAsync(state, plane, buf, width, width, 5, cudaMemcpyDefault, h->stream), "qlga_copy_rows in");
+    return QLGA_OK;
+}
+
+qlga_status qlga_exchange_rows(qlga_handle* src, int64_t ysrc, qlga_handle* dst, int64_t ydst, int64_t nrows) {
+    if (!src || !dst) return fail(QLGA_ERR_INVALID_ARG, "NULL argument%s");
+    if (src->cfg.nx != dst->cfg.nx || src->cfg.precision != dst->cfg.precision || src->cfg.ndim != dst->cfg.ndim)
+        return fail(QLGA_ERR_INVALID_ARG, "the two handles differ in nx, precision or ndim%s");
+    if (src->pending_k != dst->pending_k)
+        return fail(QLGA_ERR_INVALID_ARG, "the two handles hold their states in different forms (step them together)%s");
+    if (nrows <= 0 || ysrc < 0 || ydst < 0 || ysrc + nrows > src->cfg.ny || ydst + nrows > dst->cfg.ny)
+        return fail(QLGA_ERR_INVALID_ARG, "rows outside a lattice%s");
+    if (src == dst && ((ysrc < ydst + nrows) && (ydst < ysrc + nrows)))
+        return fail(QLGA_ERR_INVALID_ARG, "overlapping rows in one handle%s");
+    if (src->stream != dst->stream) {  // the copy waits for the source's queued work
+        cudaEvent_t ev = nullptr;
+        QLGA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "exchange event");
+        cudaError_t e = cudaEventRecord(ev, src->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+        cudaEventDestroy(ev);
+        QLGA_CUDA(e, "exchange ordering");
+    }
+    const size_t sb = site_bytes_of(src->cfg);
+    const size_t width = size_t(nrows) * size_t(src->cfg.nx) * sb;
+    const char* from = static_cast<const char*>(src->X[src->cur]) + size_t(ysrc) * size_t(src->cfg.nx) * sb;
+    char* to = static_cast<char*>(dst->X[dst->cur]) + size_t(ydst) * size_t(dst->cfg.nx) * sb;
+    QLGA_CUDA(cudaMemcpy2DAsync(to, size_t(nsites_of(dst->cfg)) * sb, from, size_t(nsites_of(src->cfg)) * sb, width, 5,
+                                cudaMemcpyDefault, dst->stream),
+              "qlga_exchange_rows");
+    if (src->stream != dst->stream) {  // the source must not overwrite its rows before the copy ends
+        cudaEvent_t ev = nullptr;
+        QLGA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "exchange event");
+        cudaError_t e = cudaEventRecord(ev, dst->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);
+        cudaEventDestroy(ev);
+        QLGA_CUDA(e, "exchange ordering");
+    }
     return QLGA_OK;
 }
 
@@ -1743,7 +1905,7 @@ const char* qlga_last_error(void) { return g_last_error.c_str(); }
 
 namespace {
 
-constexpr int kAdjMaxBlocks = 152 * 8;
+constexpr int kAdjMaxBlocks = 1216;  // capacity of the coupling partials (8 per SM on 152 SMs)
 
 struct AdjLayout {
     void* cot;
@@ -1807,7 +1969,7 @@ void adj_axis_v(qlga_handle* h, const void* gin, void* gout, const void* X, int 
 }
 
 qlga_status adj_axis(qlga_handle* h, const void* gin, void* gout, const void* X, int axis, bool vjp, double* partials) {
-    const int blocks = grid_for_block(nsites_of(h->cfg), kAdjThreads, kAdjMaxBlocks);
+    const int blocks = grid_for_block(nsites_of(h->cfg), kAdjThreads, std::min(kAdjMaxBlocks, 8 * device_sms()));
     if (h->cfg.precision == 32) {
         if (vjp) adj_axis_v<float, true>(h, gin, gout, X, axis, partials, blocks);
         else adj_axis_v<float, false>(h, gin, gout, X, axis, partials, blocks);
@@ -2201,7 +2363,7 @@ qlga_status qlga_batch_create(const qlga_batch_config* cfg, void* stream, qlga_b
         int64_t strip_rows = 0;
         for (int r = 0; r < cfg->nruns; ++r)
             if (runs[r].ny > 1) strip_rows += (runs2d[r].nx / kStep2dWarpCols) * int64_t(runs2d[r].ny);
-        const int64_t target = 152 * 12 * 2;
+        const int64_t target = int64_t(device_sms()) * 12 * 2;
         const int64_t rows = std::max<int64_t>(16, (strip_rows + target - 1) / std::max<int64_t>(target, 1));
         for (int r = 0; r < cfg->nruns; ++r) {
             if (runs[r].ny == 1) continue;

@@ -375,6 +375,10 @@ __device__ __forceinline__ void taylor_apply2(const WOp<T>& W, const cpx<T> xp[5
 // Each Horner step v <- x - (i/k) W v is one pass: W / k is formed once per k (shared by the two
 // vectors) and x is the start of every output's multiply-add chain, so the step costs no
 // operations beyond the matrix-vector product.
+#ifndef QLGA_HORNER_PINGPONG
+#define QLGA_HORNER_PINGPONG 1
+#endif
+
 template <class T>
 struct WFrameK {
     T D[5];    // diagonal of W / k
@@ -450,12 +454,6 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
     const T g2r = C.dr * rho, gz = C.dz * Fz;
     const T D[5] = {T(2) * gz - g2r, gz - g2r, -g2r, -gz - g2r, T(-2) * gz - g2r};
     const T ep0 = C.e0 * fpa, ep1 = C.e1 * fpa, R = C.R * inv_sigma2;
-    cpx<T> vp[5], vd[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        vp[i] = xp[i];
-        vd[i] = xd[i];
-    }
     auto scaled = [&](int k) {
         const T ik = inv_k(k, T(0));
         WFrameK<T> Wk;
@@ -466,6 +464,73 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
         Wk.R = R * ik;
         return Wk;
     };
+    auto finish = [&](const cpx<T> (&vp)[5], const cpx<T> (&vd)[5]) {
+        T sn, cs;
+        sin_cos(C.cphase * rho, &sn, &cs);
+        const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
+        cpx<T> q[5];  // the output phase with the frame undone
+        q[0] = cmulc(e2, ph);
+        q[1] = cmulc(e, ph);
+        q[2] = ph;
+        q[3] = cmul(e, ph);
+        q[4] = cmul(e2, ph);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            a[i] = cmul(q[i], vp[i] + vd[i]);
+            b[i] = cmul(q[i], vp[i] - vd[i]);
+        }
+    };
+#if QLGA_HORNER_PINGPONG
+    // The iterates alternate between the register sets A and B, two steps per pass, so that no
+    // step copies its result back (the copies of a loop-carried 5-vector are register moves).
+    // Steps k = K .. Kd + 1 act on psi alone (d's Horner sum has degree Kd <= K).
+    cpx<T> Ap[5], Ad[5], Bp[5], Bd[5];
+    int k = K;
+    const bool single = K > Kd;
+    if (single) {
+        horner_zframe(xp, xp, Ap, scaled(k), u);
+        for (--k; k > Kd; --k) {
+            horner_zframe(xp, Ap, Bp, scaled(k), u);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) Ap[i] = Bp[i];
+        }
+    }
+    if (k == 0) {  // Kd = 0 (rare): d keeps its zeroth-order term
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            Bp[i] = single ? Ap[i] : xp[i];
+            Bd[i] = xd[i];
+        }
+    } else {  // first step of both sums: psi from A (or x), d from x
+        const WFrameK<T> Wk = scaled(k);
+        if (single) horner_zframe(xp, Ap, Bp, Wk, u);
+        else horner_zframe(xp, xp, Bp, Wk, u);
+        horner_zframe(xd, xd, Bd, Wk, u);
+        --k;
+    }
+    for (; k >= 2; k -= 2) {  // B -> A -> B
+        WFrameK<T> Wk = scaled(k);
+        horner_zframe(xp, Bp, Ap, Wk, u);
+        horner_zframe(xd, Bd, Ad, Wk, u);
+        Wk = scaled(k - 1);
+        horner_zframe(xp, Ap, Bp, Wk, u);
+        horner_zframe(xd, Ad, Bd, Wk, u);
+    }
+    if (k == 1) {
+        const WFrameK<T> Wk = scaled(1);
+        horner_zframe(xp, Bp, Ap, Wk, u);
+        horner_zframe(xd, Bd, Ad, Wk, u);
+        finish(Ap, Ad);
+    } else {
+        finish(Bp, Bd);
+    }
+#else
+    cpx<T> vp[5], vd[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        vp[i] = xp[i];
+        vd[i] = xd[i];
+    }
     int k = K;
     for (; k > Kd; --k) {
         const WFrameK<T> Wk = scaled(k);
@@ -485,20 +550,8 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
             vd[i] = od[i];
         }
     }
-    T sn, cs;
-    sin_cos(C.cphase * rho, &sn, &cs);
-    const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
-    cpx<T> q[5];  // the output phase with the frame undone
-    q[0] = cmulc(e2, ph);
-    q[1] = cmulc(e, ph);
-    q[2] = ph;
-    q[3] = cmul(e, ph);
-    q[4] = cmul(e2, ph);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        a[i] = cmul(q[i], vp[i] + vd[i]);
-        b[i] = cmul(q[i], vp[i] - vd[i]);
-    }
+    finish(vp, vd);
+#endif
 }
 
 // FP64 kernels run the Taylor sums in the z frame too: with the FP64 tolerance the degree is

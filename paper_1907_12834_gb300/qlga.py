@@ -83,6 +83,12 @@ _SIGNATURES = {
     "qlga_get_step2d_kernel": [_H, ctypes.POINTER(ctypes.c_int32)],
     "qlga_observables_noalloc": [_CFG, _VP, _VP, _VP, ctypes.POINTER(QlgaObs)],
     "qlga_fields": [_H, _VP, ctypes.c_int],
+    "qlga_copy_rows": [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int],
+    "qlga_objective": [_H, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _VP],
+    "qlga_exchange_rows": [_H, ctypes.c_int64, _H, ctypes.c_int64, ctypes.c_int64],
+    "qlga_observable_sums": [_H, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_double)],
+    "qlga_obs_from_sums": [ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(QlgaObs)],
     "qlga_batch_state_bytes": [ctypes.POINTER(QlgaBatchConfig), ctypes.POINTER(ctypes.c_size_t)],
     "qlga_batch_create": [ctypes.POINTER(QlgaBatchConfig), _VP, ctypes.POINTER(_H)],
     "qlga_batch_load_state": [_H, _VP, ctypes.c_int],
@@ -224,6 +230,57 @@ def qlga_observables_noalloc(cfg: QlgaConfig, state_ptr: int, ref_ptr: int = 0,
                                                    _VP(ref_ptr or None), _VP(stream or None),
                                                    ctypes.byref(out)),
            "qlga_observables_noalloc")
+    return out
+
+
+def _dbl3(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def qlga_objective(h: int, x_ptr: int, level: int, g, weights=None, cot_ptr: int = 0):
+    """(values[3], dg[3] or None) of qlga_objective; the cotangent goes to cot_ptr if given."""
+    ga, gp = _dbl3(g)
+    vals = np.zeros(3)
+    dg = np.zeros(3) if weights is not None else None
+    wa, wp = _dbl3(weights) if weights is not None else (None, None)
+    _check(load_library().qlga_objective(_H(h), _VP(x_ptr), int(level), gp, wp,
+                                         vals.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         dg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if dg is not None else None,
+                                         _VP(cot_ptr or None)),
+           "qlga_objective")
+    return vals, dg
+
+
+QLGA_ROWS_OUT, QLGA_ROWS_IN = 0, 1
+
+
+def qlga_copy_rows(h: int, y0: int, nrows: int, ptr: int, direction: int):
+    _check(load_library().qlga_copy_rows(_H(h), int(y0), int(nrows), _VP(ptr), int(direction)),
+           "qlga_copy_rows")
+
+
+def qlga_exchange_rows(src: int, ysrc: int, dst: int, ydst: int, nrows: int):
+    _check(load_library().qlga_exchange_rows(_H(src), int(ysrc), _H(dst), int(ydst), int(nrows)),
+           "qlga_exchange_rows")
+
+
+def qlga_observable_sums(h: int, y0: int, y1: int, ref_ptr: int = 0) -> np.ndarray:
+    out = np.zeros(14, dtype=np.float64)
+    _check(load_library().qlga_observable_sums(_H(h), int(y0), int(y1), _VP(ref_ptr or None),
+                                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "qlga_observable_sums")
+    return out
+
+
+def qlga_obs_from_sums(sums, step: int = 0) -> QlgaObs:
+    a = np.ascontiguousarray(sums, dtype=np.float64)
+    if a.shape != (14,):
+        raise ValueError("sums must hold 14 values")
+    out = QlgaObs()
+    _check(load_library().qlga_obs_from_sums(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(step),
+                                             ctypes.byref(out)),
+           "qlga_obs_from_sums")
     return out
 
 
@@ -437,6 +494,33 @@ class Lattice:
             ref_ptr = ref.data_ptr()
         return obs_to_dict(qlga_observables(self.handle, ref_ptr))
 
+    def copy_rows_out(self, y0, nrows, out=None):
+        """Rows [y0, y0 + nrows) of the current buffer, as held, into a device tensor of
+        5 * nrows * nx sites (float32 x4 or float64 x4 per site)."""
+        torch = self._torch
+        shape = (5, int(nrows), self.shape[2], 4)
+        if out is None:
+            out = torch.empty(shape, dtype=self.tdtype, device=self.device)
+        out = require_device_tensor(out, shape, self.tdtype, self.device, "rows", writable=True)
+        qlga_copy_rows(self.handle, y0, nrows, out.data_ptr(), QLGA_ROWS_OUT)
+        return out
+
+    def copy_rows_in(self, y0, rows):
+        """Write rows [y0, y0 + rows.shape[1]) of the current buffer from a device tensor made
+        by copy_rows_out on a handle of the same nx and precision."""
+        nrows = int(rows.shape[1])
+        rows = require_device_tensor(rows, (5, nrows, self.shape[2], 4), self.tdtype, self.device,
+                                     "rows").contiguous()
+        qlga_copy_rows(self.handle, y0, nrows, rows.data_ptr(), QLGA_ROWS_IN)
+
+    def observable_sums(self, y0=0, y1=None, ref=None) -> np.ndarray:
+        """The 14 FP64 sums behind observables() over rows [y0, y1)."""
+        ref_ptr = 0
+        if ref is not None:
+            ref = require_device_tensor(ref, self.shape, self.tdtype, self.device, "ref").contiguous()
+            ref_ptr = ref.data_ptr()
+        return qlga_observable_sums(self.handle, y0, self.shape[1] if y1 is None else y1, ref_ptr)
+
     def fields(self):
         """Per-site fields, numpy (11, ny, nx): F_par, F_perp, |A00|, r, g, b, vorticity m=+2..-2."""
         out = np.empty((11, self.shape[1], self.shape[2]), dtype=self.dtype)
@@ -594,63 +678,73 @@ def evolve(x0, g, nsteps, checkpoint_every=100, kinetic_variant=0):
     return _evolve_fn.apply(x0, g, int(nsteps), int(checkpoint_every), int(kinetic_variant))
 
 
+_objective_fn = None
+
+
+def _make_objective():
+    import torch
+
+    class Objective(torch.autograd.Function):
+        """(P_level, singlet fraction, energy) of a state tensor through qlga_objective; the
+        backward pass asks the library for the cotangent of the weighted sum the incoming
+        gradient defines, and for the energy's own dependence on the couplings."""
+
+        @staticmethod
+        def forward(ctx, x, g, level):
+            lat = _lattice_for(x.shape, x.dtype, (0.0, 0.0, 0.0), 0, x.device)
+            xc = require_device_tensor(x.detach(), lat.shape, lat.tdtype, lat.device, "x").contiguous()
+            vals, _ = qlga_objective(lat.handle, xc.data_ptr(), level, g.detach().cpu().double().numpy())
+            ctx.save_for_backward(xc, g)
+            ctx.level = int(level)
+            return torch.tensor(vals, dtype=torch.float64, device=x.device)
+
+        @staticmethod
+        def backward(ctx, grad_vals):
+            xc, g = ctx.saved_tensors
+            lat = _lattice_for(xc.shape, xc.dtype, (0.0, 0.0, 0.0), 0, xc.device)
+            cot = torch.empty_like(xc)
+            w = grad_vals.detach().double().cpu().numpy()
+            _, dg = qlga_objective(lat.handle, xc.data_ptr(), ctx.level, g.detach().cpu().double().numpy(), w,
+                                   cot.data_ptr())
+            return cot, torch.tensor(dg, dtype=g.dtype, device=g.device), None
+
+    return Objective
+
+
+def objectives(x, g=(0.0, 0.0, 0.0), level=2):
+    """Tensor (P_level, singlet fraction, energy) of a CUDA state tensor (5, ny, nx, 2, 2)
+    (float64 or float32; ny = 1 is 1D), differentiable in x and in the couplings g of the energy
+    (a tensor or three floats).  Computed by the library (qlga_objective): FP64 sums; the
+    cotangent comes from the library's kernel."""
+    import torch
+    global _objective_fn
+    if _objective_fn is None:
+        _objective_fn = _make_objective()
+    if not (isinstance(x, torch.Tensor) and x.is_cuda):
+        raise TypeError("objectives need a CUDA tensor (the library computes them on the GPU)")
+    gt = g if isinstance(g, torch.Tensor) else torch.tensor([float(v) for v in g], dtype=torch.float64,
+                                                            device=x.device)
+    return _objective_fn.apply(x, gt, int(level))
+
+
 def population(x, level):
     """Objective: qubit-basis population sum |a_m|^2 + |b_m|^2 of level index `level`
-    (0..4 for m = +2..-2) of a state tensor (5, ny, nx, 2, 2)."""
-    return (x[level] * x[level]).sum()
+    (0..4 for m = +2..-2) of a CUDA state tensor (5, ny, nx, 2, 2)."""
+    return objectives(x, level=level)[0]
 
 
 def singlet_fraction(x):
-    """Objective: sum |psi^T J psi|^2 / sum rho^2 of the boson field psi = a + b of a state
+    """Objective: sum |psi^T J psi|^2 / sum rho^2 of the boson field psi = a + b of a CUDA state
     tensor (5, ny, nx, 2, 2), J with (J psi)_m = (-1)^m psi_{-m}."""
-    pr = x[:, :, :, 0, 0] + x[:, :, :, 1, 0]
-    pi = x[:, :, :, 0, 1] + x[:, :, :, 1, 1]
-    rho = (pr * pr + pi * pi).sum(0)
-    # theta = sum_m (-1)^m psi_m psi_{-m} = 2 psi_2 psi_-2 - 2 psi_1 psi_-1 + psi_0^2
-    def prod(i, j):
-        return pr[i] * pr[j] - pi[i] * pi[j], pr[i] * pi[j] + pi[i] * pr[j]
-    r20, i20 = prod(0, 4)
-    r11, i11 = prod(1, 3)
-    r00, i00 = prod(2, 2)
-    tr = 2 * r20 - 2 * r11 + r00
-    ti = 2 * i20 - 2 * i11 + i00
-    return (tr * tr + ti * ti).sum() / (rho * rho).sum()
+    return objectives(x)[1]
 
 
 def energy(x, g):
-    """Objective: the energy of the boson field psi = a + b of a state tensor (5, ny, nx, 2, 2),
-    as the library's observables define it: sum over sites of sum_axis sum_m |psi_m(j+1) -
-    psi_m(j)|^2 (periodic forward differences) + g0/2 rho^2 + g1/2 |F|^2 + g2/10 |psi^T J psi|^2.
-    g: couplings (g0, g1, g2), floats or a tensor."""
-    import math
-    pr = x[:, :, :, 0, 0] + x[:, :, :, 1, 0]
-    pi = x[:, :, :, 0, 1] + x[:, :, :, 1, 1]
-    grad = 0.0
-    for dim in (2, 1):
-        if x.shape[dim] > 1:
-            grad = grad + ((pr.roll(-1, dims=dim) - pr) ** 2 + (pi.roll(-1, dims=dim) - pi) ** 2).sum()
-    n2 = pr * pr + pi * pi
-    rho = n2.sum(0)
-    Fz = 2 * (n2[0] - n2[4]) + (n2[1] - n2[3])
-    r = math.sqrt(1.5)
-
-    def cc(i, j):  # conj(psi_i) psi_j
-        return pr[i] * pr[j] + pi[i] * pi[j], pr[i] * pi[j] - pi[i] * pr[j]
-    terms = [cc(0, 1), cc(1, 2), cc(2, 3), cc(3, 4)]
-    w = (1.0, r, r, 1.0)
-    Fpr = 2 * sum(wk * t[0] for wk, t in zip(w, terms))
-    Fpi = 2 * sum(wk * t[1] for wk, t in zip(w, terms))
-    F2 = Fz * Fz + Fpr * Fpr + Fpi * Fpi
-
-    def prod(i, j):
-        return pr[i] * pr[j] - pi[i] * pi[j], pr[i] * pi[j] + pi[i] * pr[j]
-    r20, i20 = prod(0, 4)
-    r11, i11 = prod(1, 3)
-    r00, i00 = prod(2, 2)
-    tr = 2 * r20 - 2 * r11 + r00
-    ti = 2 * i20 - 2 * i11 + i00
-    g0, g1, g2 = g[0], g[1], g[2]
-    return grad + (0.5 * g0 * rho * rho + 0.5 * g1 * F2 + 0.1 * g2 * (tr * tr + ti * ti)).sum()
+    """Objective: the energy of the boson field psi = a + b of a CUDA state tensor
+    (5, ny, nx, 2, 2), as the library's observables define it: sum over sites of sum_axis sum_m
+    |psi_m(j+1) - psi_m(j)|^2 (periodic forward differences) + g0/2 rho^2 + g1/2 |F|^2 +
+    g2/10 |psi^T J psi|^2.  g: couplings (g0, g1, g2), floats or a tensor (then differentiable)."""
+    return objectives(x, g)[2]
 
 
 # ------------------------------------------------------------------ batches of 1D lattices

@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
+import objectives_ref
 import oracle
 from paper_1907_12834_gb300 import inputs, qlga
 
@@ -208,7 +209,7 @@ def test_objective_gradient_matches_oracle():
     cfg = oracle.make_cfg(2, n, n, *w4.g)
     xn_ref = oracle.step(x0.copy(), cfg, steps)
     xt = torch.tensor(xn_ref, requires_grad=True)
-    lref = qlga.population(xt, 2) + qlga.singlet_fraction(xt)
+    lref = objectives_ref.population(xt, 2) + objectives_ref.singlet_fraction(xt)
     (cot_n,) = torch.autograd.grad(lref, xt)
     ref = cot_n.numpy().copy()
     dref = oracle.vjp_run(x0, steps, ref, cfg)

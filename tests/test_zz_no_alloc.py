@@ -47,7 +47,8 @@ def assert_same(got, want, precision):
 
 
 @pytest.mark.parametrize("precision,ndim,nx,ny", [(32, 2, 300, 257), (64, 1, 5000, 1),
-                                                  (32, 2, 1024, 1024)])
+                                                  (32, 2, 1024, 1024), (64, 2, 256, 264),
+                                                  (32, 1, 5000, 1)])
 def test_noalloc_observables_match_twice_in_a_row(precision, ndim, nx, ny):
     rng = np.random.default_rng(nx + ny + precision)
     g = (1.0, 0.8, -0.6)

@@ -426,3 +426,54 @@ def batch2d(seed: int = 1912, nruns: int = 128, eps: float = 0.1, steps: int = 2
                       32 if dtype == np.float32 else 64, np.concatenate(parts))
     w.meta["heights"] = ny.astype(np.int64)
     return w
+
+
+# --------------------------------------------------------------------------- accuracy records
+#
+# Named workloads of the accuracy record: the FP64 oracle's results for them are stored under
+# tests/golden/ (written by scripts there that call only the oracle), and the library's paths
+# are run on the same inputs and compared.
+
+LONG_HORIZON = ("config1_g_integrable_set", "config1_g_nonintegrable_set", "config2_512")
+PERTURBATION = 1e-13
+
+
+def long_horizon_workload(name):
+    """(ndim, nx, ny, couplings, steps, checkpoint interval, FP64 initial state) of a long run:
+    config 1 at full size and step count under each coupling set, and the config 2 recipe on a
+    512^2 lattice for config 2's 5000 steps."""
+    if name == "config1_g_integrable_set":       # the profiles' couplings (1, -0.5, 0.2)
+        w = config1(L=16384, precision=64)
+        return 1, 16384, 1, w.g, 20000, 1000, np.ascontiguousarray(w.state, dtype=np.float64)
+    if name == "config1_g_nonintegrable_set":    # (1, 0.8, -0.6)
+        w = config1(L=16384, precision=64, couplings=(1.0, 0.8, -0.6))
+        return 1, 16384, 1, w.g, 20000, 1000, np.ascontiguousarray(w.state, dtype=np.float64)
+    if name == "config2_512":
+        w = config2(n=512, dtype=np.float64)
+        return 2, 512, 512, w.g, 5000, 500, np.ascontiguousarray(w.state, dtype=np.float64)
+    raise KeyError(name)
+
+
+def perturbed(x0, rel=PERTURBATION, seed=2019):
+    """x0 (1 + rel xi), xi seeded standard normal: a rounding-sized change of the initial state."""
+    rng = np.random.default_rng(seed)
+    return x0 * (1.0 + rel * rng.standard_normal(x0.shape))
+
+
+def path_accuracy_workloads():
+    """The short runs behind each timed path's accuracy statement (FP64 inputs): name ->
+    dict(kind, steps, and the workload)."""
+    return {
+        "config0": {"kind": "lattice", "steps": 2000, "w": config0()},
+        "interleaved": {"kind": "lattice", "steps": 100, "w": config2(n=128, dtype=np.float64),
+                        "interleave": 1},
+        "batch1d": {"kind": "batch", "steps": 500, "w": config3(nruns=6, lmin=512, lmax=2048, dtype=np.float64)},
+        "batch2d": {"kind": "batch", "steps": 100, "w": batch2d(nruns=4, dtype=np.float64)},
+        "adjoint": {"kind": "adjoint", "steps": 100, "w": config4(n=64, separation=20, dtype=np.float64),
+                    "cotangent_seed": 1911},
+    }
+
+
+def adjoint_cotangent(shape, seed):
+    """The seeded cotangent w of the adjoint accuracy run: L = <w, x_n>."""
+    return np.random.default_rng(seed).standard_normal(shape)

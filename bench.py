@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--n", type=int, default=4096, help="lattice side")
+    p.add_argument("--precision", type=int, default=32, choices=[32, 64],
+                   help="state precision of the timed lattice (64: the FP64 path of the same workload)")
     p.add_argument("--obs-every", type=int, default=50)
     p.add_argument("--settle", type=int, default=1000, help="untimed steps before the warm-up")
     p.add_argument("--no-e2e", action="store_true")
@@ -152,26 +154,31 @@ def strip_comments(src):
     return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
 
 
-def kernel_source_hash():
+STEP_SOURCES = {32: ("qlga_step2d.cuh", "qlga_device.cuh"),
+                64: ("qlga_step2d_f64.cuh", "qlga_step2d.cuh", "qlga_device.cuh")}
+STEP_COUNTERS = {32: "step2d_f32_traffic.json", 64: "step2d_f64_counters.json"}
+
+
+def kernel_source_hash(precision=32):
     """Hash of the fused step kernel's sources, comments excluded: the committed ncu figures stay
     valid across comment edits and lapse with any change to the code."""
     h = hashlib.sha256()
-    for name in ("qlga_step2d.cuh", "qlga_device.cuh"):
+    for name in STEP_SOURCES[precision]:
         with open(os.path.join(ROOT, "paper_1907_12834_gb300", "csrc", name)) as f:
             h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 
-def recorded_step_counters():
+def recorded_step_counters(precision=32):
     """The committed ncu figures of the fused step kernel (per site), or None when the summary is
     missing or the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")
+    path = os.path.join(ROOT, "profiles", STEP_COUNTERS[precision])
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    return d if d.get("kernel_source_hash") == kernel_source_hash() else None
+    return d if d.get("kernel_source_hash") == kernel_source_hash(precision) else None
 
 
 def counters_note():
@@ -207,11 +214,39 @@ def alu_roofline(sites, kernel_ms, sms):
                     "step on the settled 2048^2 state; the pipe, not HBM, bounds the fused step"}
 
 
-def recorded_traffic(n):
+def recorded_traffic(n, precision=32):
     """DRAM bytes per launch of the fused step kernel from the committed ncu summary, scaled to an
     n x n lattice; None when the summary is missing or the kernel source changed since."""
-    d = recorded_step_counters()
+    d = recorded_step_counters(precision)
     return None if d is None else float(d["dram_bytes_per_site"]) * n * n
+
+
+def alu64_roofline(sites, kernel_ms, sms):
+    """FP64-pipe view of the fused FP64 step, by the method of alu_roofline: FP64-pipe cycles per
+    site from the ncu capture (pct of peak sustained active x smsp__cycles_active.sum / sites)
+    over the live launch duration, against one FP64-pipe cycle per SM sub-partition per cycle at
+    the maximum SM clock; beside it the FP64 arithmetic rate (DFMA = 2 flops) against the nominal
+    1.25 TFLOP/s of GB300."""
+    d = recorded_step_counters(64)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        mhz, src = 2070.0, "nominal 2070 MHz"
+    peak = 4.0 * sms * mhz * 1e6
+    if d is None or "fp64_pipe_cycles_per_site" not in d:
+        return {"bound": "alu", "achieved": None, "peak": peak, "unit": "FP64-pipe cycles/s",
+                "frac": None, "note": "no ncu figure for the current kernel source"}
+    per_site = float(d["fp64_pipe_cycles_per_site"])
+    achieved = per_site * sites / (kernel_ms * 1e-3)
+    flops = float(d["fp64_flops_per_site"]) * sites / (kernel_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "FP64-pipe cycles/s",
+            "frac": achieved / peak, "cycles_per_site": per_site,
+            "peak_source": "4 sub-partitions x %d SMs x %s" % (sms, src),
+            "fp64_tflops": flops / 1e12, "fp64_nominal_tflops": 1.25,
+            "fp64_frac_of_nominal": flops / 1.25e12,
+            "note": "FP64-pipe cycles and FP64 operations per site from an ncu capture of the fused "
+                    "FP64 step on the settled 2048^2 state"}
 
 
 def cpu_baseline(state_f64, g, budget_s, n_sub=256):
@@ -263,8 +298,9 @@ def run_gb300(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
-    w = inputs.config2(seed=replica_seed(rank), n=n)
-    lat = qlga.Lattice(2, n, n, precision=32, g=w.g, epsilon=w.eps)
+    f64 = args.precision == 64
+    w = inputs.config2(seed=replica_seed(rank), n=n, dtype=np.float64 if f64 else np.float32)
+    lat = qlga.Lattice(2, n, n, precision=args.precision, g=w.g, epsilon=w.eps)
     stream = lat.stream
     sites = n * n
 
@@ -300,9 +336,9 @@ def run_gb300(args):
     drift = {"norm_qubit_rel": abs(obs1["norm_qubit"] - obs0["norm_qubit"]) / obs0["norm_qubit"],
              "energy_rel": abs(obs1["energy"] - obs0["energy"]) / abs(obs0["energy"]),
              "steps": args.steps,
-             "note": "FP32 state, FP64 sums, over the timed steps; the qubit norm is conserved exactly by "
-                     "every step, so its drift is FP32 rounding; the energy of the discretised field is "
-                     "not an exact invariant of the QLGA step"}
+             "note": "%s state, FP64 sums, over the timed steps; the qubit norm is conserved exactly by "
+                     "every step, so its drift is rounding; the energy of the discretised field is "
+                     "not an exact invariant of the QLGA step" % ("FP64" if f64 else "FP32")}
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -325,27 +361,30 @@ def run_gb300(args):
             dist.destroy_process_group()
         return
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_SITE_F32 * sites / (kernel_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(n)
+    bytes_per_site = 2 * BYTES_PER_SITE_F32 if f64 else BYTES_PER_SITE_F32
+    achieved = bytes_per_site * sites / (kernel_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(n, 64 if f64 else 32)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     line = {
         "metric": METRIC, "value": job_rate(world, sites, args.steps, elapsed_ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Pade vortex dipoles)",
-        "config": {"workload": w.name, "lattice": [n, n], "precision": "fp32",
+        "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic (seeded Pade vortex dipoles)",
+        "config": {"workload": w.name, "lattice": [n, n], "precision": "fp64" if f64 else "fp32",
                    "couplings": list(w.g), "epsilon": w.eps, "obs_every": args.obs_every,
                    "timed_after_step": args.settle + args.warmup,
-                   "l2": "inputs larger than L2 (%.2f GB state)" % (sites * 80 / 1e9),
+                   "l2": "inputs larger than L2 (%.2f GB state)" % (sites * (160 if f64 else 80) / 1e9),
                    "parallelism": "replicas%d" % world},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": BYTES_PER_SITE_F32,
-                     "note": "the fused step is limited by FP32 FMA-pipe cycles of the potential "
-                             "(ncu --set full on the settled 2048^2 state: %s), "
-                             "not by HBM traffic" % counters_note()},
-        "alu": alu_roofline(sites, kernel_ms, torch.cuda.get_device_properties(0).multi_processor_count),
+                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_site": bytes_per_site,
+                     "note": ("the FP64 step is bound by the FP64 pipe (see alu)" if f64 else
+                              "the fused step is limited by FP32 FMA-pipe cycles of the potential "
+                              "(ncu --set full on the settled 2048^2 state: %s), "
+                              "not by HBM traffic" % counters_note())},
+        "alu": alu64_roofline(sites, kernel_ms, sms) if f64 else alu_roofline(sites, kernel_ms, sms),
         "e2e": e2e,
         "drift": drift,
         "gpu_launches": launches,

@@ -300,6 +300,19 @@ __device__ __forceinline__ int taylor_degree(T beta, T tol) {
     return K;
 }
 
+// The warp-uniform Taylor degree: the smallest K with beta^(K+1)/(K+1)! <= tol for every lane's
+// beta (>= 0).  FP32: from the warp's largest beta (positive floats order as their bit patterns),
+// so the loop runs on warp-uniform data; FP64 keeps the per-lane degree and its warp maximum.
+template <class T>
+__device__ __forceinline__ int warp_taylor_degree(T beta, T tol) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float bmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(beta) & 0x7fffffffu));
+        return taylor_degree(bmax, tol);
+    } else {
+        return warp_max_int(taylor_degree(beta, tol));
+    }
+}
+
 // y = (delta W) x, with the per-site coefficients of W
 template <class T>
 struct WOp {
@@ -375,10 +388,6 @@ __device__ __forceinline__ void taylor_apply2(const WOp<T>& W, const cpx<T> xp[5
 // Each Horner step v <- x - (i/k) W v is one pass: W / k is formed once per k (shared by the two
 // vectors) and x is the start of every output's multiply-add chain, so the step costs no
 // operations beyond the matrix-vector product.
-#ifndef QLGA_HORNER_PINGPONG
-#define QLGA_HORNER_PINGPONG 1
-#endif
-
 template <class T>
 struct WFrameK {
     T D[5];    // diagonal of W / k
@@ -480,7 +489,6 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
             b[i] = cmul(q[i], vp[i] - vd[i]);
         }
     };
-#if QLGA_HORNER_PINGPONG
     // The iterates alternate between the register sets A and B, two steps per pass, so that no
     // step copies its result back (the copies of a loop-carried 5-vector are register moves).
     // Steps k = K .. Kd + 1 act on psi alone (d's Horner sum has degree Kd <= K).
@@ -524,34 +532,6 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
     } else {
         finish(Bp, Bd);
     }
-#else
-    cpx<T> vp[5], vd[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        vp[i] = xp[i];
-        vd[i] = xd[i];
-    }
-    int k = K;
-    for (; k > Kd; --k) {
-        const WFrameK<T> Wk = scaled(k);
-        cpx<T> op[5];
-        horner_zframe(xp, vp, op, Wk, u);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) vp[i] = op[i];
-    }
-    for (; k >= 1; --k) {
-        const WFrameK<T> Wk = scaled(k);
-        cpx<T> op[5], od[5];
-        horner_zframe(xp, vp, op, Wk, u);
-        horner_zframe(xd, vd, od, Wk, u);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            vp[i] = op[i];
-            vd[i] = od[i];
-        }
-    }
-    finish(vp, vd);
-#endif
 }
 
 // FP64 kernels run the Taylor sums in the z frame too: with the FP64 tolerance the degree is
@@ -561,7 +541,9 @@ template <class T>
 constexpr bool kZframe64 = std::is_same<T, double>::value;
 
 // Apply U to the pair (a, b) of one site in place.  SPLIT_D: pick the degree for d = a - b
-// from its size relative to psi (FP32); otherwise d uses the degree of psi.  ZFRAME: run the
+// from its size relative to psi (the FP32 per-site and 1D kernels); otherwise d uses the degree
+// of psi (FP64, and the fused 2D FP32 kernels, where the one warp-uniform loop over both vectors
+// beat the saved Taylor terms: 0.80 vs 0.85 ms per 4096^2 step).  ZFRAME: run the
 // Taylor sums in the z frame (potential_tail_zframe).  The frame costs a fixed ~60 operations per
 // site and saves ~26 per vector and Taylor term, so it pays where the warp-uniform degree is about
 // 3 or more: the FP32 2D vortex states of the fused warp-strip kernels (2.4% faster at 4096^2)
@@ -592,7 +574,7 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
     const T beta = fma(C.b1, Fabs, C.b2 * rho);
     if (!(beta <= T(kBetaMax))) atomicOr(status, 1u);  // also catches NaN
     const T tol = TaylorTol<T>::value;
-    const int K = warp_max_int(taylor_degree(beta, tol));
+    const int K = warp_taylor_degree(beta, tol);
     int Kd = K;
     if (SPLIT_D) {
         T dn2 = T(0);

@@ -22,7 +22,7 @@ def committed():
 
 def test_counters_used_while_the_source_matches(monkeypatch):
     d = committed()
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: d["kernel_source_hash"])
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda precision=32: d["kernel_source_hash"])
     per_site = d["dram_bytes_per_site"]
     assert 150.0 <= per_site <= 170.0  # one read and one write of the state, plus halo re-reads
     assert bench.recorded_traffic(2048) == per_site * 2048 * 2048
@@ -34,7 +34,7 @@ def test_counters_used_while_the_source_matches(monkeypatch):
 
 
 def test_stale_counters_are_reported_as_null(monkeypatch):
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda precision=32: "0" * 16)
     assert bench.recorded_step_counters() is None
     assert bench.recorded_traffic(4096) is None
     alu = bench.alu_roofline(4096 * 4096, 0.86, 152)

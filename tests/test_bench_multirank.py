@@ -69,11 +69,11 @@ def test_recorded_counters_follow_the_kernel_source(monkeypatch):
     import json
     with open(os.path.join(ROOT, "profiles", "step2d_f32_traffic.json")) as f:
         d = json.load(f)
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: d["kernel_source_hash"])
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda precision=32: d["kernel_source_hash"])
     a = bench.alu_roofline(4096 * 4096, 0.9, 152)
     assert a["bound"] == "alu" and 0 < a["frac"] < 1.2
     assert a["frac"] == pytest.approx(d["fma_pipe_cycles_per_site"] * 4096 * 4096 / 0.9e-3 / a["peak"])
     assert bench.recorded_traffic(4096) == pytest.approx(d["dram_bytes_per_site"] * 4096 * 4096)
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda precision=32: "0" * 16)
     assert bench.recorded_traffic(4096) is None
     assert bench.alu_roofline(4096 * 4096, 0.9, 152)["frac"] is None

@@ -541,9 +541,10 @@ template <class T>
 constexpr bool kZframe64 = std::is_same<T, double>::value;
 
 // Apply U to the pair (a, b) of one site in place.  SPLIT_D: pick the degree for d = a - b
-// from its size relative to psi (the FP32 per-site and 1D kernels); otherwise d uses the degree
-// of psi (FP64, and the fused 2D FP32 kernels, where the one warp-uniform loop over both vectors
-// beat the saved Taylor terms: 0.80 vs 0.85 ms per 4096^2 step).  ZFRAME: run the
+// from its size relative to psi (the FP32 interleaved passes, where delta is 1/8 and d's degree
+// is often lower: 15% faster there, and the FP32 per-site kernels); otherwise d uses the degree
+// of psi (FP64; the fused 2D and the tiled 1D FP32 kernels, where the one warp-uniform loop over
+// both vectors beats the saved Taylor terms: 0.80 vs 0.85 ms per 4096^2 step, 2-3% on 1D).  ZFRAME: run the
 // Taylor sums in the z frame (potential_tail_zframe).  The frame costs a fixed ~60 operations per
 // site and saves ~26 per vector and Taylor term, so it pays where the warp-uniform degree is about
 // 3 or more: the FP32 2D vortex states of the fused warp-strip kernels (2.4% faster at 4096^2)

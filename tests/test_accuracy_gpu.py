@@ -66,4 +66,4 @@ def test_long_horizon_record(name):
     # two orders of magnitude: different rounding, same dynamics)
     g_gpu = np.asarray(rec["gpu_fp64_perturbed_1e-13"])
     assert np.all(g_gpu <= 100 * growth + 1e-13) and np.all(growth <= 100 * g_gpu + 1e-13)
-    assert rec["gpu_fp64_norm_drift"] <= 1e-12
+    assert rec["gpu_fp64_norm_drift"] <= 2e-15 * steps[-1] + 1e-15     # unitary to FP64 rounding

@@ -9,8 +9,9 @@ Long runs (config 1 at its full 16384 sites and 20000 steps under both coupling 
 recipe on 512^2 for 5000 steps): every checkpoint's relative L2 error against the oracle is held
 to the larger of the precision's target (1e-11 FP64, 1e-4 FP32) and what the dynamics does to
 rounding-sized differences -- the oracle's own run from a 1e-13 perturbed start grows by a factor
-amp(t) by step t, so per-step rounding u (1e-16 FP64, 1e-7 FP32 relative) injected at every one of
-t steps can reach about u t amp(t).  The numbers are printed (pytest -s) as the record."""
+amp(t) by step t, so a per-step rounding difference u injected at every one of t steps can reach
+about u t amp(t): u = 1e-15 in FP64 (the oracle's own step is unitary to about 5e-16 per step,
+its U coming from a Jacobi eigendecomposition), 1e-7 in FP32.  The numbers are printed (pytest -s) as the record."""
 import json
 import os
 import sys
@@ -58,7 +59,7 @@ def test_long_horizon_record(name):
     steps = np.asarray(rec["steps"], dtype=np.float64)
     growth = np.asarray(rec["oracle_perturbed_1e-13"])
     amp = np.maximum.accumulate(growth / inputs.PERTURBATION)
-    for prec, u, target in ((64, 1e-16, 1e-11), (32, 1e-7, 1e-4)):
+    for prec, u, target in ((64, 1e-15, 1e-11), (32, 1e-7, 1e-4)):
         err = np.asarray(rec["gpu_fp%d_vs_oracle" % prec])
         bound = np.maximum(target, u * np.maximum(steps, 1) * amp)
         assert np.all(err <= bound), (prec, err.tolist(), bound.tolist())

@@ -157,7 +157,7 @@ __device__ __forceinline__ int build_w(const cpx<T> psi[5], const PotConst<T>& C
     const T Fabs = sqrt(fma(Fz, Fz, norm2(Fp)));
     const T beta = fma(C.b1, Fabs, C.b2 * rho);
     if (!(beta <= T(kBetaMax))) atomicOr(status, 1u);
-    const int K = warp_max_int(taylor_degree(beta, TaylorTol<T>::value));
+    const int K = warp_taylor_degree(beta, TaylorTol<T>::value);
     const T g2r = C.dr * rho;
     const T gz = C.dz * Fz;
     W.D[0] = T(2) * gz - g2r;

@@ -63,8 +63,8 @@ def test_long_horizon_record(name):
         err = np.asarray(rec["gpu_fp%d_vs_oracle" % prec])
         bound = np.maximum(target, u * np.maximum(steps, 1) * amp)
         assert np.all(err <= bound), (prec, err.tolist(), bound.tolist())
-    # the GPU FP64 run shows the same amplification of a 1e-13 start as the oracle's (within
-    # two orders of magnitude: different rounding, same dynamics)
+    # the GPU FP64 run amplifies a 1e-13 start no more than the oracle does: the oracle's
+    # difference carries its own (larger) rounding, amplified alike, on top of the perturbation
     g_gpu = np.asarray(rec["gpu_fp64_perturbed_1e-13"])
-    assert np.all(g_gpu <= 100 * growth + 1e-13) and np.all(growth <= 100 * g_gpu + 1e-13)
+    assert np.all(g_gpu <= 2 * growth + 1e-13), (g_gpu.tolist(), growth.tolist())
     assert rec["gpu_fp64_norm_drift"] <= 2e-15 * steps[-1] + 1e-15     # unitary to FP64 rounding

@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-paths", action="store_true",
                    help="skip the FP64 / batched / adjoint / interleaved comparison runs")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the paths' accuracy runs against the stored oracle results")
     return p.parse_args()
 
 
@@ -555,6 +557,8 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
                    "(forward with checkpoints + recompute + pull-back); norm_identity_error = "
                    "|dL/dx0 - x0| / |x0| for L = |x_n|^2 / 2; 'accuracy' of a path: its kernels run "
                    "on a short case of the path's recipe against the FP64 oracle's stored results")
+    if args.no_accuracy:
+        return out
     acc = path_accuracy(torch, qlga, inputs) or {}
     lh = long_horizon_record(torch, qlga, inputs)
     for key, src in (("config0_fp64_1d", "config0_fp64_1d"), ("interleaved_fp32_2d", "interleaved_fp32_2d"),

@@ -121,7 +121,9 @@ __global__ void k_convert_layout(const T* src, T* dst, int64_t npairs) {
 
 // U on every site, in place.  All lanes of a warp run the potential (the Taylor degree is a
 // warp-wide maximum); lanes past the end work on zeros and store nothing.
-template <class T, bool SPLIT>
+// HELD_PQ (FP32 only): store the result as (P, Q) = (a + bt, a - bt), the form in which the fused
+// 2D FP32 step holds a state pending K (qlga_step2d.cuh); else in the resident layout (a, bt).
+template <class T, bool SPLIT, bool HELD_PQ = false>
 __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotConst<T> PC,
                                                         unsigned* status) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -136,7 +138,14 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
             for (int m = 0; m < 5; ++m) a[m] = b[m] = {T(0), T(0)};
         }
         potential_site<T, SPLIT, kZframe64<T>>(a, b, PC, T(1), T(0.5), status);
-        if (active) SiteIO<T>::store(X, nsites, site, a, b);
+        if (active) {
+            if constexpr (HELD_PQ) {
+#pragma unroll
+                for (int m = 0; m < 5; ++m) reinterpret_cast<float4*>(X)[m * nsites + site] = pq_of(a[m], b[m]);
+            } else {
+                SiteIO<T>::store(X, nsites, site, a, b);
+            }
+        }
     }
 }
 
@@ -851,11 +860,11 @@ int grid_for(int64_t n, int cap = 0) {
 
 PotParams pot_params(const qlga_config& c, double delta) { return PotParams{c.g0, c.g1, c.g2, delta}; }
 
-template <class T>
+template <class T, bool HELD_PQ = false>
 qlga_status launch_potential(qlga_handle* h, void* buf, double delta) {
     const int64_t n = nsites_of(h->cfg);
     const int nt = block_for(n);
-    k_potential<T, std::is_same<T, float>::value><<<grid_for_block(n, nt), nt, 0, h->stream>>>(
+    k_potential<T, std::is_same<T, float>::value, HELD_PQ><<<grid_for_block(n, nt), nt, 0, h->stream>>>(
         static_cast<T*>(buf), n, PotConst<T>(pot_params(h->cfg, delta)), h->status);
     QLGA_CUDA(cudaGetLastError(), "k_potential launch");
     h->launches += 1;
@@ -887,6 +896,18 @@ qlga_status launch_axis(qlga_handle* h, const void* in, void* out, int axis, boo
 
 qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
     return h->cfg.precision == 32 ? launch_potential<float>(h, buf, delta) : launch_potential<double>(h, buf, delta);
+}
+
+bool step2d_uses_fused(const qlga_handle* h);
+
+// Whether this handle holds its states pending K in the (P, Q) form of the fused FP32 step.
+bool held_pq(const qlga_handle* h) { return h->cfg.precision == 32 && step2d_uses_fused(h); }
+
+// U on a true state, leaving it held pending K (X = U psi, true state K X): the first half of a
+// step, in the form the handle's kinetic pass reads.
+qlga_status launch_pot_held(qlga_handle* h, void* buf) {
+    if (held_pq(h)) return launch_potential<float, true>(h, buf, 1.0);
+    return launch_pot(h, buf, 1.0);
 }
 
 // One interleaved axis pass (U^(1/(4 ndim)) before each of the axis's four blocks), in -> out.
@@ -1125,9 +1146,12 @@ bool step2d_uses_fused(const qlga_handle* h) {
 
 // Apply the full kinetic operator: in -> out (out may not alias in).  2D uses `mid` for the
 // x pass.  With pot, U follows the last axis (the fused step).
-qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot) {
+// out = [U] K in.  held: `in` is a state held pending K (the handle's held form; the fused FP32
+// step reads (P, Q)); otherwise a true state in the resident layout, which the two-pass form
+// takes on a lattice that holds (P, Q).
+qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot, bool held = true) {
     if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
-    if (step2d_uses_fused(h)) {
+    if (step2d_uses_fused(h) && (held || !held_pq(h))) {
         const int err = h->cfg.precision == 32
             ? step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny,
                                 h->cfg.kinetic_variant, pot, PotConst<float>(pot_params(h->cfg, 1.0)), h->status,
@@ -1525,7 +1549,7 @@ qlga_status qlga_step(qlga_handle* h, int64_t n) {
                 h->cur ^= 1;
             }
         } else if (!h->pending_k) {
-            s = launch_pot(h, h->X[h->cur], 1.0);  // X = U psi, true state K X
+            s = launch_pot_held(h, h->X[h->cur]);  // X = U psi, true state K X
             if (s != QLGA_OK) return s;
             h->pending_k = true;
         } else {
@@ -1550,7 +1574,7 @@ qlga_status qlga_apply_kinetic(qlga_handle* h) {
     if (!h) return fail(QLGA_ERR_INVALID_ARG, "handle is NULL%s");
     qlga_status s = materialize(h);
     if (s != QLGA_OK) return s;
-    s = kinetic_into(h, h->X[h->cur], h->X[1 - h->cur], h->tmp, false);
+    s = kinetic_into(h, h->X[h->cur], h->X[1 - h->cur], h->tmp, false, false);  // a true state
     if (s != QLGA_OK) return s;
     h->cur ^= 1;
     return QLGA_OK;
@@ -1809,6 +1833,9 @@ qlga_status qlga_set_step2d_mode(qlga_handle* h, int32_t mode) {
         return fail(QLGA_ERR_INVALID_ARG, "mode must be QLGA_STEP2D_AUTO, _FUSED or _TWO_PASS%s");
     if (mode == QLGA_STEP2D_FUSED && (h->cfg.ndim != 2 || !step2d_f32_supported(h->cfg.nx, h->cfg.ny)))
         return fail(QLGA_ERR_UNSUPPORTED, "the fused 2D kernel needs a 2D lattice with nx a multiple of 32%s");
+    // a state held pending K is read out first: the new form may hold it differently
+    qlga_status s = materialize(h);
+    if (s != QLGA_OK) return s;
     cudaStreamSynchronize(h->stream);
     graphs_release(h);
     h->step2d_mode = mode;
@@ -2086,7 +2113,7 @@ qlga_status qlga_adjoint_backward(qlga_handle* h, int64_t nsteps, int64_t checkp
         if (len > 1) {
             void *y = L.w1, *y2 = L.w2;
             QLGA_CUDA(cudaMemcpyAsync(y, slot0, nb, cudaMemcpyDeviceToDevice, h->stream), "segment copy");
-            s = launch_pot(h, y, 1.0);
+            s = launch_pot_held(h, y);
             if (s != QLGA_OK) return s;
             for (int64_t i = 1; i < len; ++i) {
                 s = kinetic_into(h, y, L.slots + L.state * size_t(i), tmp, false);
@@ -2231,9 +2258,16 @@ __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchT
         potential_site<T, sizeof(T) == 4, kZframe64<T>>(a, b, C, T(1), T(0.5), status);
         __syncwarp();
         if (j < run.L) {
+            // 2D runs (FP32) go on with the fused step, which holds them pending K as (P, Q)
+            const bool pq = sizeof(T) == 4 && run.ny > 1;
 #pragma unroll
-            for (int m = 0; m < 5; ++m)
-                store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re, a[m].im, -b[m].im, b[m].re);
+            for (int m = 0; m < 5; ++m) {
+                if (pq)
+                    store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re - b[m].im, a[m].im + b[m].re,
+                                   a[m].re + b[m].im, a[m].im - b[m].re);
+                else
+                    store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re, a[m].im, -b[m].im, b[m].re);
+            }
         }
     }
 }

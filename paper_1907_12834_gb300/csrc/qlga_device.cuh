@@ -5,7 +5,9 @@
 //    of that level as (a.re, a.im, bt.re, bt.im) with bt = i*b.  One float4 (FP32) or two double2
 //    (FP64) per site and plane, so a warp reading 32 consecutive sites of a plane reads 512 or
 //    1024 contiguous bytes.  The C ABI's layout (a.re, a.im, b.re, b.im) is converted on load and
-//    read-out only; SiteIO / load_pair return (a, b).
+//    read-out only; SiteIO / load_pair return (a, b).  A 2D FP32 state held pending K for the
+//    fused step is stored as (P, Q) = (a + bt, a - bt) instead (qlga_step2d.cuh): its x stencil
+//    has fewer taps in that basis.
 //  * Inside the kinetic operator the pair is carried as (a, bt) with bt = i*b.  In that basis the
 //    collide C = 1/2 [[1-i, 1+i], [1+i, 1-i]] of a kinetic block (Sec. VII.B) becomes the scalar
 //    (1-i)/2 times the real matrix [[1, 1], [-1, 1]], so a collide costs four real additions per

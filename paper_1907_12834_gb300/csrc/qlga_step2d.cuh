@@ -10,14 +10,15 @@
 //      rows ahead of use; warps synchronise only within themselves (__syncwarp), never with each
 //      other, and the halo columns are read by both neighbouring warps (from L2);
 //   2. x axis: the nine-point stencil of one axis (integer coefficients derived at compile time
-//      from the block definition) reads the lane's column and its 8 neighbours from shared
-//      memory;
+//      from the block definition, taken in the (P, Q) = (a + bt, a - bt) basis the held state is
+//      stored in: 24 taps per level instead of 32) reads the lane's column and its 8 neighbours
+//      from shared memory;
 //   3. y axis: the four blocks I'_2 I'_2 I'_1 I'_1 run as a streaming pipeline down the column:
 //      each block keeps one row of history (the unshifted qubit after the first collide and the
 //      shifted qubit after the second), so the y axis costs 8 collides of 4 additions per level,
 //      has no halo recomputation, and lags the input by 4 rows;
-//   4. the potential unitary acts on the finished site, and the site is written with five 16-byte
-//      stores that are coalesced across the warp.
+//   4. the potential unitary acts on the finished site, and the site is written as (P, Q) with five
+//      16-byte stores that are coalesced across the warp.
 // The first 8 rows of a range only fill the pipeline (the dependency cone is +-4 rows).
 //
 // The kinetic arithmetic is unnormalised: every collide drops its scalar prefactor, so the site
@@ -124,14 +125,46 @@ __device__ __forceinline__ float2 tap(float2 x, float2 acc) {
     return p_fma<STYLE>(float(COEF), x, acc);
 }
 
+// A 2D FP32 state held pending K on the fused path stores each pair as (P, Q) = (a + bt, a - bt)
+// instead of (a, bt).  With (a, bt) = ((P + Q) / 2, (P - Q) / 2) the nine-point x stencil acting
+// on (P, Q) has the integer taps M_k = g_k [[1, 1], [1, -1]] / 2 (every g_k has entries of equal
+// parity in each row, so the halves are exact): 24 nonzero taps per level instead of 32 in the
+// (a, bt) basis, the fewest of any small integer basis.  The output of the x axis is (a, bt) as
+// before; the store of a step converts back to (P, Q).
+constexpr KinStencil make_stencil_pq(int variant) {
+    const KinStencil g = make_stencil(variant);
+    KinStencil S{};
+    for (int dst = 0; dst < 2; ++dst)
+        for (int k = 0; k < 9; ++k) {
+            S.g[dst][0][k] = (g.g[dst][0][k] + g.g[dst][1][k]) / 2;  // coefficient of P
+            S.g[dst][1][k] = (g.g[dst][0][k] - g.g[dst][1][k]) / 2;  // coefficient of Q
+        }
+    return S;
+}
+constexpr bool stencil_pq_exact(int variant) {
+    const KinStencil g = make_stencil(variant);
+    for (int dst = 0; dst < 2; ++dst)
+        for (int k = 0; k < 9; ++k)
+            if ((g.g[dst][0][k] + g.g[dst][1][k]) % 2 != 0) return false;
+    return true;
+}
+static_assert(stencil_pq_exact(0) && stencil_pq_exact(1), "the (P, Q) stencil taps must be integers");
+constexpr KinStencil kStencilPQ[2] = {make_stencil_pq(0), make_stencil_pq(1)};
+
+// (P, Q) of a pair (a, b): P = a + i b, Q = a - i b, as one float4
+__device__ __forceinline__ float4 pq_of(cpx<float> a, cpx<float> b) {
+    return make_float4(a.re - b.im, a.im + b.re, a.re + b.im, a.im - b.re);
+}
+
+// One tap of the x stencil on a staged (P, Q) pair.
 template <int VARIANT, int K, int STYLE>
 __device__ __forceinline__ void stencil_tap(const float4 v, float2& xa, float2& xbt) {
-    constexpr KinStencil S = kStencil[VARIANT];
-    const float2 a = make_float2(v.x, v.y), bt = make_float2(v.z, v.w);
-    xa = tap<S.g[0][0][K], STYLE>(a, xa);
-    xa = tap<S.g[0][1][K], STYLE>(bt, xa);
-    xbt = tap<S.g[1][0][K], STYLE>(a, xbt);
-    xbt = tap<S.g[1][1][K], STYLE>(bt, xbt);
+    constexpr KinStencil S = kStencilPQ[VARIANT];
+    const float2 P = make_float2(v.x, v.y), Q = make_float2(v.z, v.w);
+    xa = tap<S.g[0][0][K], STYLE>(P, xa);
+    xa = tap<S.g[0][1][K], STYLE>(Q, xa);
+    xbt = tap<S.g[1][0][K], STYLE>(P, xbt);
+    xbt = tap<S.g[1][1][K], STYLE>(Q, xbt);
 }
 
 // Launch geometry: warps of 32 columns, 4 warps per CTA, each warp with its own ring.
@@ -223,8 +256,9 @@ __device__ __forceinline__ void strip_kinetic_rows(const float* __restrict__ in,
     cp_async_wait<0>();
 }
 
-// One warp's share of a step: K on the strip, then (POT) the potential unitary, and the store of
-// rows [y_begin, y_end) in the resident layout.  POT = false stores K X alone.
+// One warp's share of a step: K on the strip (input held pending K as (P, Q)), then (POT) the
+// potential unitary and the store of rows [y_begin, y_end) as (P, Q) again.  POT = false stores
+// K X alone, the true state, in the resident layout (a, bt).
 template <int VARIANT, bool POT, int STYLE>
 __device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float* __restrict__ out, int nx,
                                              int ny, int x0, int y_begin, int y_end, const PotConst<float>& PC,
@@ -247,13 +281,15 @@ __device__ __forceinline__ void step2d_strip(const float* __restrict__ in, float
             }
             const int64_t site = int64_t(y) * nx + x0 + lane;
 #pragma unroll
-            for (int m = 0; m < 5; ++m)
-                out4[int64_t(m) * nsites + site] = make_float4(oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+            for (int m = 0; m < 5; ++m)  // POT: held pending K again, as (P, Q); else the true state
+                out4[int64_t(m) * nsites + site] =
+                    POT ? pq_of(oa[m], ob[m]) : make_float4(oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
         });
 }
 
 // The kernel.  POT = false applies the kinetic operator alone (out = K X), used to read out a
 // state held pending K.  Warp gw of the grid takes strip gw % strips of row chunk gw / strips.
+// The input is always a state held pending K, stored as (P, Q).
 template <int VARIANT, bool POT = true, int STYLE = QLGA_STEP2D_STYLE>
 __global__ void __launch_bounds__(kStep2dWarpsPerCta * 32, 3)
     k_step2d_f32(const float* __restrict__ in, float* __restrict__ out, int nx, int ny, int chunks,

@@ -711,7 +711,6 @@ def path_accuracy(torch, qlga, inputs):
 
 
 E2E_REPEATS = 3
-E2E_REPEATS = 3
 
 
 def run_e2e(lat, state, args, torch, qlga, sites):

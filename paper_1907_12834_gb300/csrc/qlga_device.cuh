@@ -400,11 +400,12 @@ struct WFrameK {
 template <class T>
 __device__ __forceinline__ void horner_zframe(const cpx<T> x[5], const cpx<T> v[5], cpx<T> o[5], const WFrameK<T>& Wk,
                                               const cpx<T> u[5]) {
-    cpx<T> t0 = cmul(u[0], v[0]), t1 = cmul(u[1], v[1]);
+    cpx<T> t0 = cmul(u[0], v[0]);  // one accumulation chain (two split chains cost two more additions)
+    t0 = cfma(u[1], v[1], t0);
     t0 = cfma(u[2], v[2], t0);
-    t1 = cfma(u[3], v[3], t1);
+    t0 = cfma(u[3], v[3], t0);
     t0 = cfma(u[4], v[4], t0);
-    const cpx<T> t = Wk.R * (t0 + t1);  // (s^dagger v) times the singlet coefficient
+    const cpx<T> t = Wk.R * t0;  // (s^dagger v) times the singlet coefficient
     // y_i = D_i v_i + conj(u_i) t + (off-diagonal neighbours); o = x - i y:
     // o.re = x.re + y.im, o.im = x.im - y.re
 #pragma unroll

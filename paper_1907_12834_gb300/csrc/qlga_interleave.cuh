@@ -166,30 +166,26 @@ __global__ void __launch_bounds__(kIlvXThreads) k_interleave_x(const T* __restri
 
 // One streaming block along y for one level (input row n -> output row n - 1, in place); the
 // state keeps the unshifted qubit after the first collide (yo) and the shifted qubit after the
-// second (wc) from the previous row.  C = 1 shifts bt, C = 0 shifts a.
+// second (wc) from the previous row.  C = 1 shifts bt, C = 0 shifts a.  The new yo is formed from
+// the inputs only after the old one has been used, so that the loop-carried value can keep its
+// register from row to row.
 template <class T, int FIRST>
 __device__ __forceinline__ void ilv_stream(int c, cpx<T>& a, cpx<T>& bt, cpx<T>& yo, cpx<T>& wc) {
-    cpx<T> ya = a, ybt = bt;
-    ilv_collide<T, FIRST>(ya, ybt);
-    cpx<T> za, zbt;
-    if (c == 0) {
-        za = ya;
-        zbt = yo;
-        yo = ybt;
-    } else {
-        za = yo;
-        zbt = ybt;
-        yo = ya;
-    }
-    ilv_collide<T, 0>(za, zbt);
-    if (c == 0) {
-        a = wc;
-        bt = zbt;
-        wc = za;
-    } else {
-        a = za;
+    const cpx<T> ia = a, ibt = bt;
+    if (c == 1) {
+        const cpx<T> ybt = FIRST == 0 ? ibt - ia : ia + ibt;
+        const cpx<T> wa = yo + ybt, wbt = ybt - yo;  // second collide of (yo, ybt)
+        yo = FIRST == 0 ? ia + ibt : ia - ibt;
+        a = wa;
         bt = wc;
-        wc = zbt;
+        wc = wbt;
+    } else {
+        const cpx<T> ya = FIRST == 0 ? ia + ibt : ia - ibt;
+        const cpx<T> wa = ya + yo, wbt = yo - ya;  // second collide of (ya, yo)
+        yo = FIRST == 0 ? ibt - ia : ia + ibt;
+        a = wc;
+        bt = wbt;
+        wc = wa;
     }
 }
 

@@ -157,7 +157,7 @@ def strip_comments(src):
 
 
 STEP_SOURCES = {32: ("qlga_step2d.cuh", "qlga_device.cuh"),
-                64: ("qlga_step2d_f64.cuh", "qlga_step2d.cuh", "qlga_device.cuh")}
+                64: ("qlga_step2d_f64.cuh", "qlga_interleave.cuh", "qlga_step2d.cuh", "qlga_device.cuh")}
 STEP_COUNTERS = {32: "step2d_f32_traffic.json", 64: "step2d_f64_counters.json"}
 
 

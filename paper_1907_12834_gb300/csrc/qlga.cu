@@ -119,10 +119,14 @@ __global__ void k_convert_layout(const T* src, T* dst, int64_t npairs) {
     }
 }
 
+__device__ __forceinline__ void put_pq(float* X, int64_t pair, cpx<float> a, cpx<float> b) {
+    reinterpret_cast<float4*>(X)[pair] = pq_of(a, b);
+}
+
 // U on every site, in place.  All lanes of a warp run the potential (the Taylor degree is a
 // warp-wide maximum); lanes past the end work on zeros and store nothing.
-// HELD_PQ (FP32 only): store the result as (P, Q) = (a + bt, a - bt), the form in which the fused
-// 2D FP32 step holds a state pending K (qlga_step2d.cuh); else in the resident layout (a, bt).
+// HELD_PQ: store the result as (P, Q) = (a + bt, a - bt), the form in which the fused 2D steps
+// hold a state pending K (qlga_step2d.cuh); else in the resident layout (a, bt).
 template <class T, bool SPLIT, bool HELD_PQ = false>
 __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotConst<T> PC,
                                                         unsigned* status) {
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
         if (active) {
             if constexpr (HELD_PQ) {
 #pragma unroll
-                for (int m = 0; m < 5; ++m) reinterpret_cast<float4*>(X)[m * nsites + site] = pq_of(a[m], b[m]);
+                for (int m = 0; m < 5; ++m) put_pq(X, m * nsites + site, a[m], b[m]);
             } else {
                 SiteIO<T>::store(X, nsites, site, a, b);
             }
@@ -900,13 +904,14 @@ qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
 
 bool step2d_uses_fused(const qlga_handle* h);
 
-// Whether this handle holds its states pending K in the (P, Q) form of the fused FP32 step.
-bool held_pq(const qlga_handle* h) { return h->cfg.precision == 32 && step2d_uses_fused(h); }
+// Whether this handle holds its states pending K in the (P, Q) form of the fused 2D steps.
+bool held_pq(const qlga_handle* h) { return step2d_uses_fused(h); }
 
 // U on a true state, leaving it held pending K (X = U psi, true state K X): the first half of a
 // step, in the form the handle's kinetic pass reads.
 qlga_status launch_pot_held(qlga_handle* h, void* buf) {
-    if (held_pq(h)) return launch_potential<float, true>(h, buf, 1.0);
+    if (held_pq(h))
+        return h->cfg.precision == 32 ? launch_potential<float, true>(h, buf, 1.0) : launch_potential<double, true>(h, buf, 1.0);
     return launch_pot(h, buf, 1.0);
 }
 

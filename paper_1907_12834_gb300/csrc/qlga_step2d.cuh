@@ -123,8 +123,8 @@ __device__ __forceinline__ float2 tap(float2 x, float2 acc) {
     return p_fma<STYLE>(float(COEF), x, acc);
 }
 
-// A 2D FP32 state held pending K on the fused path stores each pair as (P, Q) = (a + bt, a - bt)
-// instead of (a, bt).  With (a, bt) = ((P + Q) / 2, (P - Q) / 2) the nine-point x stencil acting
+// A 2D state held pending K on the fused path (FP32 and FP64) stores each pair as
+// (P, Q) = (a + bt, a - bt) instead of (a, bt).  With (a, bt) = ((P + Q) / 2, (P - Q) / 2) the nine-point x stencil acting
 // on (P, Q) has the integer taps M_k = g_k [[1, 1], [1, -1]] / 2 (every g_k has entries of equal
 // parity in each row, so the halves are exact): 24 nonzero taps per level instead of 32 in the
 // (a, bt) basis, the fewest of any small integer basis.  The output of the x axis is (a, bt) as

@@ -5,7 +5,10 @@
 // nine-point x stencil from shared memory, runs the four y blocks as a register pipeline, then
 // the potential unitary, and stores the site.  In FP64 every arithmetic instruction occupies the
 // FP64 pipe (2 FMA per SM per cycle on GB300), so the y pipeline -- 8 collides of 4 additions per
-// level instead of a second nine-point stencil -- and the single pass are what matter.
+// level instead of a second nine-point stencil -- and the single pass are what matter, and so
+// does the held form: states pending K are stored as (P, Q) = (a + bt, a - bt) as in FP32, whose
+// x stencil has 24 nonzero integer taps per level against 32 in (a, bt); zero taps are skipped at
+// compile time and +-1 taps are additions.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,6 +19,33 @@
 
 namespace qlga {
 
+// Store a pair (a, b) as (P, Q) = (a + i b, a - i b) at pair index `pair` of the resident layout
+// (two double2; the FP32 form is one float4, pq_of in qlga_step2d.cuh).
+__device__ __forceinline__ void put_pq(double* X, int64_t pair, cpx<double> a, cpx<double> b) {
+    double2* p = reinterpret_cast<double2*>(X) + 2 * pair;
+    p[0] = make_double2(a.re - b.im, a.im + b.re);
+    p[1] = make_double2(a.re + b.im, a.im - b.re);
+}
+
+// acc + c x for a compile-time integer c (0: nothing, +-1: an addition)
+template <int C>
+__device__ __forceinline__ double tap64(double x, double acc) {
+    if constexpr (C == 0) return acc;
+    else if constexpr (C == 1) return acc + x;
+    else if constexpr (C == -1) return acc - x;
+    else return fma(double(C), x, acc);
+}
+
+// One tap of the x stencil on a staged (P, Q) pair (re and im of each).
+template <int VARIANT, int K>
+__device__ __forceinline__ void stencil_tap64(const double2 P, const double2 Q, cpx<double>& xa, cpx<double>& xbt) {
+    constexpr KinStencil S = kStencilPQ[VARIANT];
+    xa.re = tap64<S.g[0][1][K]>(Q.x, tap64<S.g[0][0][K]>(P.x, xa.re));
+    xa.im = tap64<S.g[0][1][K]>(Q.y, tap64<S.g[0][0][K]>(P.y, xa.im));
+    xbt.re = tap64<S.g[1][1][K]>(Q.x, tap64<S.g[1][0][K]>(P.x, xbt.re));
+    xbt.im = tap64<S.g[1][1][K]>(Q.y, tap64<S.g[1][0][K]>(P.y, xbt.im));
+}
+
 constexpr int kStep2d64WarpsPerCta = 2;
 constexpr int kStep2d64SmemBytes =
     kStep2d64WarpsPerCta * kStep2dStages * 5 * kStep2dWarpRowSites * 32;  // double pairs
@@ -25,7 +55,6 @@ __global__ void __launch_bounds__(kStep2d64WarpsPerCta * 32)
     k_step2d_f64(const double* __restrict__ in, double* __restrict__ out, int nx, int ny, int chunks,
                  PotConst<double> PC, unsigned* status) {
     extern __shared__ double2 dring[];  // [warp][kStages][5][kStep2dWarpRowSites][2]
-    constexpr KinStencil S = kStencil[VARIANT];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strips = nx / kStep2dWarpCols;
     const int gw = blockIdx.x * kStep2d64WarpsPerCta + w;
@@ -91,19 +120,18 @@ __global__ void __launch_bounds__(kStep2d64WarpsPerCta * 32)
         cpx<double> oa[5], ob[5];
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
-            // x axis: nine-point stencil (x16, unnormalised) in the (a, bt) basis
+            // x axis: nine-point stencil (x16, unnormalised) from the held (P, Q) pairs to (a, bt)
             cpx<double> xa = {0.0, 0.0}, xbt = {0.0, 0.0};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const double2 pa = row[2 * (m * kStep2dWarpRowSites + lane + k)];
-                const double2 pb = row[2 * (m * kStep2dWarpRowSites + lane + k) + 1];
-                const double caa = S.g[0][0][k], cab = S.g[0][1][k];
-                const double cba = S.g[1][0][k], cbb = S.g[1][1][k];
-                xa.re = fma(caa, pa.x, fma(cab, pb.x, xa.re));
-                xa.im = fma(caa, pa.y, fma(cab, pb.y, xa.im));
-                xbt.re = fma(cba, pa.x, fma(cbb, pb.x, xbt.re));
-                xbt.im = fma(cba, pa.y, fma(cbb, pb.y, xbt.im));
-            }
+            const double2* p = row + 2 * (m * kStep2dWarpRowSites + lane);
+            stencil_tap64<VARIANT, 0>(p[0], p[1], xa, xbt);
+            stencil_tap64<VARIANT, 1>(p[2], p[3], xa, xbt);
+            stencil_tap64<VARIANT, 2>(p[4], p[5], xa, xbt);
+            stencil_tap64<VARIANT, 3>(p[6], p[7], xa, xbt);
+            stencil_tap64<VARIANT, 4>(p[8], p[9], xa, xbt);
+            stencil_tap64<VARIANT, 5>(p[10], p[11], xa, xbt);
+            stencil_tap64<VARIANT, 6>(p[12], p[13], xa, xbt);
+            stencil_tap64<VARIANT, 7>(p[14], p[15], xa, xbt);
+            stencil_tap64<VARIANT, 8>(p[16], p[17], xa, xbt);
             // y axis: I'_2 I'_2 then I'_1 I'_1 as a streaming pipeline (x16, unnormalised)
             ilv_stream<double, VARIANT>(1, xa, xbt, yo[0][m], wc[0][m]);
             ilv_stream<double, VARIANT>(1, xa, xbt, yo[1][m], wc[1][m]);
@@ -124,10 +152,14 @@ __global__ void __launch_bounds__(kStep2d64WarpsPerCta * 32)
             }
             const int64_t site = int64_t(y_begin + r - 8) * nx + x0 + lane;
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {  // resident layout: (a, bt = i b)
-                double2* p = out2 + 2 * (int64_t(m) * nsites + site);
-                p[0] = make_double2(oa[m].re, oa[m].im);
-                p[1] = make_double2(-ob[m].im, ob[m].re);
+            for (int m = 0; m < 5; ++m) {
+                if (POT) {  // held pending K again, as (P, Q)
+                    put_pq(out, int64_t(m) * nsites + site, oa[m], ob[m]);
+                } else {  // the true state, in the resident layout (a, bt = i b)
+                    double2* p = out2 + 2 * (int64_t(m) * nsites + site);
+                    p[0] = make_double2(oa[m].re, oa[m].im);
+                    p[1] = make_double2(-ob[m].im, ob[m].re);
+                }
             }
         }
     }

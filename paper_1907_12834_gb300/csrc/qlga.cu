@@ -160,7 +160,6 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
                                                            T* __restrict__ out, int64_t nx,
                                                            int64_t ny, int axis, PotConst<T> PC,
                                                            unsigned* status) {
-    constexpr KinStencil S = kStencil[VARIANT];
     const int64_t nsites = nx * ny;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x; base < nsites; base += stride) {
@@ -185,18 +184,13 @@ __global__ void __launch_bounds__(kThreads) k_kinetic_axis(const T* __restrict__
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             cpx<T> acc_a = {T(0), T(0)}, acc_bt = {T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
+            static_for<9>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
                 cpx<T> a, b;
                 load_pair<T>(in, nsites, m, nb[k], a, b);
                 const cpx<T> bt = {-b.im, b.re};  // bt = i b
-                const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
-                const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
-                acc_a.re = fma(caa, a.re, fma(cab, bt.re, acc_a.re));
-                acc_a.im = fma(caa, a.im, fma(cab, bt.im, acc_a.im));
-                acc_bt.re = fma(cba, a.re, fma(cbb, bt.re, acc_bt.re));
-                acc_bt.im = fma(cba, a.im, fma(cbb, bt.im, acc_bt.im));
-            }
+                kin_tap<VARIANT, k>(a, bt, acc_a, acc_bt);
+            });
             const T sc = T(0.0625);
             oa[m] = {sc * acc_a.re, sc * acc_a.im};
             ob[m] = {sc * acc_bt.im, -sc * acc_bt.re};  // b = -i bt

@@ -407,17 +407,12 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? 4 : 1) k_adjoint
 #pragma unroll
         for (int m = 0; m < 5; ++m) {
             cpx<T> acc_a = {T(0), T(0)}, acc_bt = {T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
+            static_for<9>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
                 cpx<T> a, bt;
                 load_resident(gin, nsites, m, nb[k], a, bt);
-                const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
-                const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
-                acc_a.re = fma(caa, a.re, fma(cab, bt.re, acc_a.re));
-                acc_a.im = fma(caa, a.im, fma(cab, bt.im, acc_a.im));
-                acc_bt.re = fma(cba, a.re, fma(cbb, bt.re, acc_bt.re));
-                acc_bt.im = fma(cba, a.im, fma(cbb, bt.im, acc_bt.im));
-            }
+                kin_tap4<S.g[0][0][k], S.g[0][1][k], S.g[1][0][k], S.g[1][1][k]>(a, bt, acc_a, acc_bt);
+            });
             const T sc = T(0.0625);
             ga[m] = {sc * acc_a.re, sc * acc_a.im};
             gb[m] = {sc * acc_bt.im, -sc * acc_bt.re};  // b = -i bt

@@ -67,20 +67,14 @@ __device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T
 template <class T, int VARIANT>
 __device__ __forceinline__ void batch_kinetic_at(const Pair4<T>* src, int stride, int p, cpx<T> oa[5],
                                                  cpx<T> ob[5]) {
-    constexpr KinStencil S = kStencil[VARIANT];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
-#pragma unroll
-        for (int kk = 0; kk < 9; ++kk) {
+        static_for<9>([&](auto kc) {
+            constexpr int kk = decltype(kc)::value;
             const Pair4<T> q = src[m * stride + p + kk];
-            const T caa = T(S.g[0][0][kk]), cab = T(S.g[0][1][kk]);
-            const T cba = T(S.g[1][0][kk]), cbb = T(S.g[1][1][kk]);
-            xa.re = fma(caa, q.v[0], fma(cab, q.v[2], xa.re));
-            xa.im = fma(caa, q.v[1], fma(cab, q.v[3], xa.im));
-            xbt.re = fma(cba, q.v[0], fma(cbb, q.v[2], xbt.re));
-            xbt.im = fma(cba, q.v[1], fma(cbb, q.v[3], xbt.im));
-        }
+            kin_tap<VARIANT, kk>(cpx<T>{q.v[0], q.v[1]}, cpx<T>{q.v[2], q.v[3]}, xa, xbt);
+        });
         oa[m] = xa;                 // x16, unnormalised
         ob[m] = {xbt.im, -xbt.re};  // b = -i bt
     }

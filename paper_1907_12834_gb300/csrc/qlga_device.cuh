@@ -165,26 +165,55 @@ constexpr KinStencil make_stencil(int variant) {
 
 constexpr KinStencil kStencil[2] = {make_stencil(0), make_stencil(1)};
 
+// f(std::integral_constant<int, 0>) .. f(std::integral_constant<int, N - 1>), in order
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
+// acc + c x for a compile-time integer c: nothing for 0 (fma(0, x, acc) is not folded under IEEE
+// rules), an addition or a subtraction for +-1 (the same rounding as the fma)
+template <int C, class T>
+__device__ __forceinline__ T ktap(T x, T acc) {
+    if constexpr (C == 0) return acc;
+    else if constexpr (C == 1) return acc + x;
+    else if constexpr (C == -1) return acc - x;
+    else return fma(T(C), x, acc);
+}
+
+// One tap of an (a, bt) stencil on one neighbour, coefficients (AA, AB; BA, BB):
+// acc_a += AA a + AB bt and acc_bt += BA a + BB bt, each component as fma(A., a, fma(.B, bt, acc)).
+template <int AA, int AB, int BA, int BB, class T>
+__device__ __forceinline__ void kin_tap4(const cpx<T>& a, const cpx<T>& bt, cpx<T>& acc_a, cpx<T>& acc_bt) {
+    acc_a.re = ktap<AA>(a.re, ktap<AB>(bt.re, acc_a.re));
+    acc_a.im = ktap<AA>(a.im, ktap<AB>(bt.im, acc_a.im));
+    acc_bt.re = ktap<BA>(a.re, ktap<BB>(bt.re, acc_bt.re));
+    acc_bt.im = ktap<BA>(a.im, ktap<BB>(bt.im, acc_bt.im));
+}
+// Tap K of the kinetic stencil of VARIANT
+template <int VARIANT, int K, class T>
+__device__ __forceinline__ void kin_tap(const cpx<T>& a, const cpx<T>& bt, cpx<T>& acc_a, cpx<T>& acc_bt) {
+    constexpr KinStencil S = kStencil[VARIANT];
+    kin_tap4<S.g[0][0][K], S.g[0][1][K], S.g[1][0][K], S.g[1][1][K]>(a, bt, acc_a, acc_bt);
+}
+
 // Kinetic operator of one axis at one site from its 9 neighbours along the axis.
 // nb[k][m]: (a, b) of level m at offset k - 4.  Returns (a, b) of the output, scaled exactly.
 template <class T, int VARIANT>
 __device__ __forceinline__ void kinetic_axis_site(const cpx<T> (*nba)[5], const cpx<T> (*nbb)[5],
                                                   cpx<T> oa[5], cpx<T> ob[5]) {
-    constexpr KinStencil S = kStencil[VARIANT];
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         cpx<T> acc_a = {T(0), T(0)}, acc_bt = {T(0), T(0)};
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const cpx<T> a = nba[k][m];
+        static_for<9>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
             const cpx<T> bt = {-nbb[k][m].im, nbb[k][m].re};  // bt = i b
-            const T caa = T(S.g[0][0][k]), cab = T(S.g[0][1][k]);
-            const T cba = T(S.g[1][0][k]), cbb = T(S.g[1][1][k]);
-            acc_a.re = fma(caa, a.re, fma(cab, bt.re, acc_a.re));
-            acc_a.im = fma(caa, a.im, fma(cab, bt.im, acc_a.im));
-            acc_bt.re = fma(cba, a.re, fma(cbb, bt.re, acc_bt.re));
-            acc_bt.im = fma(cba, a.im, fma(cbb, bt.im, acc_bt.im));
-        }
+            kin_tap<VARIANT, k>(nba[k][m], bt, acc_a, acc_bt);
+        });
         const T s = T(0.0625);
         oa[m] = {s * acc_a.re, s * acc_a.im};
         ob[m] = {s * acc_bt.im, -s * acc_bt.re};  // b = -i bt

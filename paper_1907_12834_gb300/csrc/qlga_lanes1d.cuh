@@ -72,7 +72,6 @@ template <class T, int VARIANT, int LPS>
 __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T* __restrict__ out, int L,
                                                      PotConst<T> C, unsigned* status) {
     static_assert(LPS == 5 || LPS == 10, "five or ten lanes per site");
-    constexpr KinStencil S = kStencil[VARIANT];
     constexpr int SPW = 30 / LPS;  // sites per warp
     const int lane = threadIdx.x;
     const int q = lane < 30 ? lane / LPS : SPW - 1;
@@ -86,19 +85,14 @@ __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T
 
     // K on level m: the nine-point stencil of the axis (16 times the true value)
     cpx<T> xa = {T(0), T(0)}, xbt = {T(0), T(0)};
-#pragma unroll
-    for (int kk = 0; kk < 9; ++kk) {
+    static_for<9>([&](auto kc) {
+        constexpr int kk = decltype(kc)::value;
         int jj = j - 4 + kk;
         jj %= L;
         jj = jj < 0 ? jj + L : jj;
         const Pair4<T> p = load_raw_pair(in, int64_t(m) * L + jj);
-        const T caa = T(S.g[0][0][kk]), cab = T(S.g[0][1][kk]);
-        const T cba = T(S.g[1][0][kk]), cbb = T(S.g[1][1][kk]);
-        xa.re = fma(caa, p.v[0], fma(cab, p.v[2], xa.re));
-        xa.im = fma(caa, p.v[1], fma(cab, p.v[3], xa.im));
-        xbt.re = fma(cba, p.v[0], fma(cbb, p.v[2], xbt.re));
-        xbt.im = fma(cba, p.v[1], fma(cbb, p.v[3], xbt.im));
-    }
+        kin_tap<VARIANT, kk>(cpx<T>{p.v[0], p.v[1]}, cpx<T>{p.v[2], p.v[3]}, xa, xbt);
+    });
     const cpx<T> a = xa, b = {xbt.im, -xbt.re};  // b = -i bt
     const cpx<T> psi = a + b, d = a - b;
 

@@ -153,6 +153,22 @@ __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, Po
     }
 }
 
+// (a, bt) -> (P, Q) = (a + bt, a - bt) for npairs pairs of the resident layout, in -> out.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pq_of_resident(const T* __restrict__ in, T* __restrict__ out,
+                                                             int64_t npairs) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+        const T* p = in + 4 * i;
+        const T ar = p[0], ai = p[1], br = p[2], bi = p[3];
+        T* q = out + 4 * i;
+        q[0] = ar + br;
+        q[1] = ai + bi;
+        q[2] = ar - br;
+        q[3] = ai - bi;
+    }
+}
+
 // out = [U o] K_axis(in): the nine-point kinetic stencil of one axis (derived at compile time
 // from the block definition), optionally followed by the potential unitary.
 template <class T, int VARIANT, bool POT>
@@ -898,8 +914,9 @@ qlga_status launch_pot(qlga_handle* h, void* buf, double delta) {
 
 bool step2d_uses_fused(const qlga_handle* h);
 
-// Whether this handle holds its states pending K in the (P, Q) form of the fused 2D steps.
-bool held_pq(const qlga_handle* h) { return step2d_uses_fused(h); }
+// Whether this handle holds its states pending K in the (P, Q) form: 1D lattices and the fused
+// 2D steps (the two-pass 2D form holds (a, bt)).
+bool held_pq(const qlga_handle* h) { return h->cfg.ndim == 1 || step2d_uses_fused(h); }
 
 // U on a true state, leaving it held pending K (X = U psi, true state K X): the first half of a
 // step, in the form the handle's kinetic pass reads.
@@ -1149,7 +1166,19 @@ bool step2d_uses_fused(const qlga_handle* h) {
 // step reads (P, Q)); otherwise a true state in the resident layout, which the two-pass form
 // takes on a lattice that holds (P, Q).
 qlga_status kinetic_into(qlga_handle* h, const void* in, void* out, void* mid, bool pot, bool held = true) {
-    if (h->cfg.ndim == 1) return tile_1d(h, in, out, pot);
+    if (h->cfg.ndim == 1) {
+        if (!held) {  // a true state: the 1D kernels read (P, Q), so write that form into mid first
+            const int64_t np = 5 * nsites_of(h->cfg);
+            if (h->cfg.precision == 32)
+                k_pq_of_resident<float><<<grid_for(np), kThreads, 0, h->stream>>>(static_cast<const float*>(in), static_cast<float*>(mid), np);
+            else
+                k_pq_of_resident<double><<<grid_for(np), kThreads, 0, h->stream>>>(static_cast<const double*>(in), static_cast<double*>(mid), np);
+            QLGA_CUDA(cudaGetLastError(), "k_pq_of_resident launch");
+            h->launches += 1;
+            in = mid;
+        }
+        return tile_1d(h, in, out, pot);
+    }
     if (step2d_uses_fused(h) && (held || !held_pq(h))) {
         const int err = h->cfg.precision == 32
             ? step2d_f32_launch(static_cast<const float*>(in), static_cast<float*>(out), h->cfg.nx, h->cfg.ny,
@@ -2257,16 +2286,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_potential(T* X, const BatchT
         potential_site<T, sizeof(T) == 4, kZframe64<T>>(a, b, C, T(1), T(0.5), status);
         __syncwarp();
         if (j < run.L) {
-            // 2D runs (FP32) go on with the fused step, which holds them pending K as (P, Q)
-            const bool pq = sizeof(T) == 4 && run.ny > 1;
+            // every run (1D tiles, 2D warp strips) holds its state pending K as (P, Q)
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                if (pq)
-                    store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re - b[m].im, a[m].im + b[m].re,
-                                   a[m].re + b[m].im, a[m].im - b[m].re);
-                else
-                    store_raw_pair(X, run.base + int64_t(m) * run.L + j, a[m].re, a[m].im, -b[m].im, b[m].re);
-            }
+            for (int m = 0; m < 5; ++m) store_raw_pq(X, run.base + int64_t(m) * run.L + j, a[m], b[m]);
         }
     }
 }

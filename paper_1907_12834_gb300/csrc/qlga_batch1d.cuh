@@ -61,9 +61,26 @@ __device__ __forceinline__ void store_raw_pair(T* X, int64_t pair, T a0, T a1, T
     }
 }
 
+// A 1D state held pending K (single lattices and the 1D runs of a batch, both precisions) stores
+// each pair as (P, Q) = (a + bt, a - bt), like the fused 2D steps: the nine-point stencil of the
+// axis then has 24 nonzero integer taps per level instead of 32 (kStencilPQ, qlga_step2d.cuh).
+
+// Tap K of the kinetic stencil of VARIANT on a neighbour held as (P, Q): (a, bt) accumulators.
+template <int VARIANT, int K, class T>
+__device__ __forceinline__ void kin_tap_pq(const cpx<T>& P, const cpx<T>& Q, cpx<T>& acc_a, cpx<T>& acc_bt) {
+    constexpr KinStencil S = kStencilPQ[VARIANT];
+    kin_tap4<S.g[0][0][K], S.g[0][1][K], S.g[1][0][K], S.g[1][1][K]>(P, Q, acc_a, acc_bt);
+}
+
+// (P, Q) = (a + i b, a - i b) of a pair (a, b), stored at pair index `pair` of the resident layout
+template <class T>
+__device__ __forceinline__ void store_raw_pq(T* X, int64_t pair, cpx<T> a, cpx<T> b) {
+    store_raw_pair(X, pair, a.re - b.im, a.im + b.re, a.re + b.im, a.im - b.re);
+}
+
 // The kinetic operator (nine-point stencil of the axis, Sec. VII.B) at staged column p of src,
-// a shared-memory array of 5 planes of `stride` pairs: the site whose neighbourhood is columns
-// p .. p + 8.  Returns (a, b) 16 times the true value (the collides' factors dropped).
+// a shared-memory array of 5 planes of `stride` pairs held as (P, Q): the site whose neighbourhood
+// is columns p .. p + 8.  Returns (a, b) 16 times the true value (the collides' factors dropped).
 template <class T, int VARIANT>
 __device__ __forceinline__ void batch_kinetic_at(const Pair4<T>* src, int stride, int p, cpx<T> oa[5],
                                                  cpx<T> ob[5]) {
@@ -73,7 +90,7 @@ __device__ __forceinline__ void batch_kinetic_at(const Pair4<T>* src, int stride
         static_for<9>([&](auto kc) {
             constexpr int kk = decltype(kc)::value;
             const Pair4<T> q = src[m * stride + p + kk];
-            kin_tap<VARIANT, kk>(cpx<T>{q.v[0], q.v[1]}, cpx<T>{q.v[2], q.v[3]}, xa, xbt);
+            kin_tap_pq<VARIANT, kk>(cpx<T>{q.v[0], q.v[1]}, cpx<T>{q.v[2], q.v[3]}, xa, xbt);
         });
         oa[m] = xa;                 // x16, unnormalised
         ob[m] = {xbt.im, -xbt.re};  // b = -i bt
@@ -81,7 +98,8 @@ __device__ __forceinline__ void batch_kinetic_at(const Pair4<T>* src, int stride
 }
 
 // One fused step (POT) or the kinetic operator alone, for the tiles of a batch; with STEPS = 2,
-// two fused steps.  A CTA of W threads computes W * SPT consecutive sites of one run per pass
+// two fused steps.  The input is held pending K as (P, Q); POT stores (P, Q) again, the kinetic
+// operator alone the true state (a, bt).  A CTA of W threads computes W * SPT consecutive sites of one run per pass
 // (thread t owns sites t, t + W, ...).  The tile and its periodic halo of 4 * STEPS sites on
 // each side are staged in shared memory with 16-byte cp.async copies, all in flight at once.
 // STEPS = 2 (temporal blocking): the first step covers the tile and 4 halo sites per side, into
@@ -142,7 +160,8 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
             // degree for d on the 1D scattering batches and on config 1)
             potential_site<T, false, kZframe64<T>>(oa, ob, C, T(1.0 / 256.0), T(0.5 / 16.0), status);
 #pragma unroll
-            for (int m = 0; m < 5; ++m) mid[m][p] = Pair4<T>{{oa[m].re, oa[m].im, -ob[m].im, ob[m].re}};
+            for (int m = 0; m < 5; ++m)  // held pending K, as (P, Q)
+                mid[m][p] = Pair4<T>{{oa[m].re - ob[m].im, oa[m].im + ob[m].re, oa[m].re + ob[m].im, oa[m].im - ob[m].re}};
         }
         __syncthreads();
     }
@@ -169,8 +188,12 @@ __global__ void __launch_bounds__(W) k_batch_step(const T* __restrict__ in, T* _
         }
         if (tt < TOUT && j < L) {
 #pragma unroll
-            for (int m = 0; m < 5; ++m)
-                store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+            for (int m = 0; m < 5; ++m) {
+                if (POT)  // held pending K again, as (P, Q)
+                    store_raw_pq(out, run.base + int64_t(m) * L + j, oa[m], ob[m]);
+                else  // the true state, (a, bt)
+                    store_raw_pair(out, run.base + int64_t(m) * L + j, oa[m].re, oa[m].im, -ob[m].im, ob[m].re);
+            }
         }
     }
 }

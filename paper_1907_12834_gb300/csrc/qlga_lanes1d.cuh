@@ -8,7 +8,8 @@
 // recursion, so each lane's chain of dependent work is half as long).  Lanes 30 and 31 repeat
 // lanes 0 and 1 of the last site and store nothing.
 //   - the kinetic operator K (Sec. VII.B) acts on each level separately: each lane applies the
-//     nine-point stencil of its own level;
+//     nine-point stencil of its own level to the state held pending K as (P, Q) (qlga_batch1d.cuh),
+//     and the lane stores its level of the new held state as (P, Q);
 //   - U = e^{-i delta c} exp(-i delta W) needs the site's rho, F_z, F_+ and the singlet vector
 //     s_m = (-1)^m conj(psi_{-m}): sums over the site's five psi lanes and shuffles from the lane
 //     of level -m;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T
         jj %= L;
         jj = jj < 0 ? jj + L : jj;
         const Pair4<T> p = load_raw_pair(in, int64_t(m) * L + jj);
-        kin_tap<VARIANT, kk>(cpx<T>{p.v[0], p.v[1]}, cpx<T>{p.v[2], p.v[3]}, xa, xbt);
+        kin_tap_pq<VARIANT, kk>(cpx<T>{p.v[0], p.v[1]}, cpx<T>{p.v[2], p.v[3]}, xa, xbt);  // held (P, Q)
     });
     const cpx<T> a = xa, b = {xbt.im, -xbt.re};  // b = -i bt
     const cpx<T> psi = a + b, d = a - b;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T
     sin_cos(C.cphase * rho, &sn, &cs);
     const cpx<T> ph = {cs * out_scale, -sn * out_scale};  // e^{-i delta c} / (2 sigma)
     const cpx<T> na = cmul(ph, vp + vd), nb = cmul(ph, vp - vd);
-    if (store) store_raw_pair(out, int64_t(m) * L + j, na.re, na.im, -nb.im, nb.re);
+    if (store) store_raw_pq(out, int64_t(m) * L + j, na, nb);  // held pending K again, as (P, Q)
 }
 
 }  // namespace qlga

@@ -459,13 +459,82 @@ __device__ __forceinline__ void horner_zframe(const cpx<T> x[5], const cpx<T> v[
     }
 }
 
+// Steps k = K .. K - Kin + 1 of the two Horner recursions of potential_tail_zframe (psi and d
+// in the frame, both of degree K) in FP32, for the FP64 kernels; the iterate after them goes to
+// (vp, vd) in FP64, and the remaining steps k = K - Kin .. 1 run in FP64 on the exact x.  An error
+// e in that iterate reaches the result multiplied by (delta W)^k0 / k0! (k0 = K - Kin >= 1 outer
+// steps), at most beta^k0 / k0! |e|; potential_site takes k0 with beta^k0 / k0! <= 2^-31, so the
+// FP32 rounding of the inner steps (a few 2^-24 of |x|) stays below the FP64 rounding of the step.
+// GB300 runs FP32 at 64 times the FP64 rate.
+__device__ __forceinline__ void zframe_inner_fp32(const cpx<double> xp[5], const cpx<double> xd[5],
+                                                  const cpx<double> u[5], const double D[5], double ep0,
+                                                  double ep1, double R, int K, int Kin, cpx<double> vp[5],
+                                                  cpx<double> vd[5]) {
+    cpx<float> xpf[5], xdf[5], uf[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        xpf[i] = {float(xp[i].re), float(xp[i].im)};
+        xdf[i] = {float(xd[i].re), float(xd[i].im)};
+        uf[i] = {float(u[i].re), float(u[i].im)};
+    }
+    float Df[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Df[i] = float(D[i]);
+    const float e0f = float(ep0), e1f = float(ep1), Rf = float(R);
+    auto scaledf = [&](int k) {
+        const float ik = inv_k(k, 0.f);
+        WFrameK<float> Wk;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Wk.D[i] = Df[i] * ik;
+        Wk.e0 = e0f * ik;
+        Wk.e1 = e1f * ik;
+        Wk.R = Rf * ik;
+        return Wk;
+    };
+    cpx<float> Ap[5], Ad[5], Bp[5], Bd[5];
+    int k = K;
+    {
+        const WFrameK<float> Wk = scaledf(k);
+        horner_zframe(xpf, xpf, Bp, Wk, uf);
+        horner_zframe(xdf, xdf, Bd, Wk, uf);
+    }
+    --k;
+    const int kend = K - Kin;  // the last FP32 step is kend + 1
+    for (; k >= kend + 2; k -= 2) {  // B -> A -> B
+        WFrameK<float> Wk = scaledf(k);
+        horner_zframe(xpf, Bp, Ap, Wk, uf);
+        horner_zframe(xdf, Bd, Ad, Wk, uf);
+        Wk = scaledf(k - 1);
+        horner_zframe(xpf, Ap, Bp, Wk, uf);
+        horner_zframe(xdf, Ad, Bd, Wk, uf);
+    }
+    if (k == kend + 1) {
+        const WFrameK<float> Wk = scaledf(k);
+        horner_zframe(xpf, Bp, Ap, Wk, uf);
+        horner_zframe(xdf, Bd, Ad, Wk, uf);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            vp[i] = {double(Ap[i].re), double(Ap[i].im)};
+            vd[i] = {double(Ad[i].re), double(Ad[i].im)};
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            vp[i] = {double(Bp[i].re), double(Bp[i].im)};
+            vd[i] = {double(Bd[i].re), double(Bd[i].im)};
+        }
+    }
+}
+
 // The end of potential_site in the z frame: the Taylor sums of exp(-i delta W) on psi (degree K) and d
 // (degree Kd <= K) in the z frame, then a = U(psi + d)/2, b = U(psi - d)/2.  Fp = F_+ and the
 // other inputs as in potential_site.
+// FP64: the first Kin steps (k = K .. K - Kin + 1) of the two sums run in FP32 (see
+// zframe_inner_fp32); Kin = 0 in FP32.
 template <class T>
 __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], const cpx<T> psi[5], const cpx<T> d[5],
                                                       cpx<T> Fp, T rho, T Fz, int K, int Kd, const PotConst<T>& C,
-                                                      T inv_sigma2, T out_scale) {
+                                                      T inv_sigma2, T out_scale, int Kin = 0) {
     const T fp2 = norm2(Fp);
     cpx<T> e = {T(1), T(0)};
     T fpa = T(0);  // |F_+|; below the smallest normal number it is taken as 0 (its terms are far below rounding)
@@ -527,6 +596,13 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
     cpx<T> Ap[5], Ad[5], Bp[5], Bd[5];
     int k = K;
     const bool single = K > Kd;
+    if constexpr (std::is_same<T, double>::value) {
+        if (Kin > 0) {  // warp-uniform; FP64 d takes psi's degree (Kd = K)
+            zframe_inner_fp32(xp, xd, u, D, ep0, ep1, R, K, Kin, Bp, Bd);
+            k = K - Kin;  // the next step; the iterate is in B
+            goto outer;
+        }
+    }
     if (single) {
         horner_zframe(xp, xp, Ap, scaled(k), u);
         for (--k; k > Kd; --k) {
@@ -548,6 +624,7 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
         horner_zframe(xd, xd, Bd, Wk, u);
         --k;
     }
+outer:
     for (; k >= 2; k -= 2) {  // B -> A -> B
         WFrameK<T> Wk = scaled(k);
         horner_zframe(xp, Bp, Ap, Wk, u);
@@ -622,7 +699,14 @@ __device__ __forceinline__ void potential_site(cpx<T> a[5], cpx<T> b[5], const P
         Kd = warp_max_int(k);
     }
     if constexpr (ZFRAME) {
-        potential_tail_zframe<T>(a, b, psi, d, Fp, rho, Fz, K, Kd, C, inv_sigma2, out_scale);
+        int Kin = 0;
+        if constexpr (std::is_same<T, double>::value) {
+            // the outer FP64 steps k0: the smallest k0 >= 1 with beta^k0 / k0! <= 2^-31 on every
+            // lane; the terms of higher order run in FP32 (zframe_inner_fp32)
+            const int k0 = warp_max_int(taylor_degree(beta, 4.656612873077393e-10) + 1);
+            Kin = K > k0 ? K - k0 : 0;
+        }
+        potential_tail_zframe<T>(a, b, psi, d, Fp, rho, Fz, K, Kd, C, inv_sigma2, out_scale, Kin);
         return;
     }
     WOp<T> W;

@@ -596,35 +596,37 @@ __device__ __forceinline__ void potential_tail_zframe(cpx<T> a[5], cpx<T> b[5], 
     cpx<T> Ap[5], Ad[5], Bp[5], Bd[5];
     int k = K;
     const bool single = K > Kd;
+    bool inner_done = false;
     if constexpr (std::is_same<T, double>::value) {
         if (Kin > 0) {  // warp-uniform; FP64 d takes psi's degree (Kd = K)
             zframe_inner_fp32(xp, xd, u, D, ep0, ep1, R, K, Kin, Bp, Bd);
             k = K - Kin;  // the next step; the iterate is in B
-            goto outer;
+            inner_done = true;
         }
     }
-    if (single) {
-        horner_zframe(xp, xp, Ap, scaled(k), u);
-        for (--k; k > Kd; --k) {
-            horner_zframe(xp, Ap, Bp, scaled(k), u);
+    if (!inner_done) {
+        if (single) {
+            horner_zframe(xp, xp, Ap, scaled(k), u);
+            for (--k; k > Kd; --k) {
+                horner_zframe(xp, Ap, Bp, scaled(k), u);
 #pragma unroll
-            for (int i = 0; i < 5; ++i) Ap[i] = Bp[i];
+                for (int i = 0; i < 5; ++i) Ap[i] = Bp[i];
+            }
         }
-    }
-    if (k == 0) {  // Kd = 0 (rare): d keeps its zeroth-order term
+        if (k == 0) {  // Kd = 0 (rare): d keeps its zeroth-order term
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            Bp[i] = single ? Ap[i] : xp[i];
-            Bd[i] = xd[i];
+            for (int i = 0; i < 5; ++i) {
+                Bp[i] = single ? Ap[i] : xp[i];
+                Bd[i] = xd[i];
+            }
+        } else {  // first step of both sums: psi from A (or x), d from x
+            const WFrameK<T> Wk = scaled(k);
+            if (single) horner_zframe(xp, Ap, Bp, Wk, u);
+            else horner_zframe(xp, xp, Bp, Wk, u);
+            horner_zframe(xd, xd, Bd, Wk, u);
+            --k;
         }
-    } else {  // first step of both sums: psi from A (or x), d from x
-        const WFrameK<T> Wk = scaled(k);
-        if (single) horner_zframe(xp, Ap, Bp, Wk, u);
-        else horner_zframe(xp, xp, Bp, Wk, u);
-        horner_zframe(xd, xd, Bd, Wk, u);
-        --k;
     }
-outer:
     for (; k >= 2; k -= 2) {  // B -> A -> B
         WFrameK<T> Wk = scaled(k);
         horner_zframe(xp, Bp, Ap, Wk, u);

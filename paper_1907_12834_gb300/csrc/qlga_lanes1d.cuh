@@ -135,12 +135,45 @@ __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T
     W.u = (m & 1) ? cpx<T>{-pm.re, -pm.im} : pm;       // u_m = (-1)^m psi_{-m} = conj(s_m)
     W.R = C.R * inv_sigma2;
 
-    // Horner: v <- x + (-i / k) W v, k = K .. 1 (d from k = Kd)
+    // Horner: v <- x + (-i / k) W v, k = K .. 1 (d from k = Kd).  FP64: the inner steps
+    // k = K .. k0 + 1 run in FP32 and the k0 outer ones in FP64 on the exact x, as in
+    // zframe_inner_fp32 (beta^k0 / k0! <= 2^-31 on every lane, k0 >= 1), so that the FP32 rounding
+    // of the inner iterate reaches the result below the FP64 rounding of the step.
+    int k = K;
+    [[maybe_unused]] WLane<float> Wf;
+    [[maybe_unused]] int k0 = K;
+    if constexpr (std::is_same<T, double>::value) {
+        k0 = warp_max_int(taylor_degree(beta, 4.656612873077393e-10) + 1);
+        k0 = k0 < K ? k0 : K;
+        Wf.D = float(W.D);
+        Wf.up = {float(W.up.re), float(W.up.im)};
+        Wf.dn = {float(W.dn.re), float(W.dn.im)};
+        Wf.u = {float(W.u.re), float(W.u.im)};
+        Wf.R = float(W.R);
+        Wf.gb = W.gb;
+        Wf.m = W.m;
+    }
+    auto to_f = [](cpx<T> z) { return cpx<float>{float(z.re), float(z.im)}; };
+    auto to_t = [](cpx<float> z) { return cpx<T>{T(z.re), T(z.im)}; };
     cpx<T> vp, vd;
     if (LPS == 5) {
         vp = psi;
         vd = d;
-        for (int k = K; k >= 1; --k) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (K > k0) {  // warp-uniform; FP64 d takes psi's degree (Kd = K)
+                const cpx<float> xpf = to_f(psi), xdf = to_f(d);
+                cpx<float> vpf = xpf, vdf = xdf;
+                for (; k > k0; --k) {
+                    const float ik = inv_k(k, 0.f);
+                    const cpx<float> wp = Wf.apply(vpf), wd = Wf.apply(vdf);
+                    vpf = {fmaf(ik, wp.im, xpf.re), fmaf(-ik, wp.re, xpf.im)};
+                    vdf = {fmaf(ik, wd.im, xdf.re), fmaf(-ik, wd.re, xdf.im)};
+                }
+                vp = to_t(vpf);
+                vd = to_t(vdf);
+            }
+        }
+        for (; k >= 1; --k) {
             const T ik = inv_k(k, T(0));
             const cpx<T> wp = W.apply(vp);
             if (k <= Kd) {  // warp-uniform
@@ -153,7 +186,19 @@ __global__ void __launch_bounds__(32) k_step1d_lanes(const T* __restrict__ in, T
         const cpx<T> x = chain == 0 ? psi : d;
         const int kmax = chain == 0 ? K : Kd;
         cpx<T> v = x;
-        for (int k = K; k >= 1; --k) {  // every lane applies W (its shuffles take the whole warp)
+        if constexpr (std::is_same<T, double>::value) {
+            if (K > k0) {  // warp-uniform; FP64: kmax = K on both chains
+                const cpx<float> xf = to_f(x);
+                cpx<float> vf = xf;
+                for (; k > k0; --k) {
+                    const float ik = inv_k(k, 0.f);
+                    const cpx<float> w = Wf.apply(vf);
+                    vf = {fmaf(ik, w.im, xf.re), fmaf(-ik, w.re, xf.im)};
+                }
+                v = to_t(vf);
+            }
+        }
+        for (; k >= 1; --k) {  // every lane applies W (its shuffles take the whole warp)
             const T ik = inv_k(k, T(0));
             const cpx<T> w = W.apply(v);
             if (k <= kmax) v = {fma(ik, w.im, x.re), fma(-ik, w.re, x.im)};

@@ -119,6 +119,8 @@ __global__ void k_convert_layout(const T* src, T* dst, int64_t npairs) {
     }
 }
 
+// Store a pair (a, b) as (P, Q) = (a + i b, a - i b) at pair index `pair` of the resident layout
+// (one float4; the FP64 form is in qlga_step2d_f64.cuh).
 __device__ __forceinline__ void put_pq(float* X, int64_t pair, cpx<float> a, cpx<float> b) {
     reinterpret_cast<float4*>(X)[pair] = pq_of(a, b);
 }
@@ -975,8 +977,8 @@ struct EventPair {
 // run of launches of `steps` fused steps on `stream`; even k step one free buffer into another and
 // odd k step back, as the real run alternates its two buffers (launches that all read one buffer
 // and write another timed the 1D shapes in a different order than the real run: the tuner chose a
-// shape 8% slower than the best on the 16384-site lattice).  Direct: a
-// warm-up launch, then two timed ones on `stream`.  Graphed (where the steps will be replayed
+// shape 8% slower than the best on the 16384-site lattice).  Direct: a warm-up launch, then two
+// timed ones on `stream`.  Graphed (where the steps will be replayed
 // from graphs, which hide the host's launch gaps; such lattices take microseconds per step):
 // kTuneGraphSteps steps captured into a graph on the capture stream cs, one warm-up replay, then
 // three timed replays.

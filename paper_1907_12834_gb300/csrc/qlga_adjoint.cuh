@@ -141,7 +141,7 @@ __device__ __forceinline__ void horner_upper(const cpx<T> w[5], const cpx<T> e[5
 // The forward step's W at a site (as potential_site builds it, unscaled input) and its degree.
 template <class T>
 __device__ __forceinline__ int build_w(const cpx<T> psi[5], const PotConst<T>& C, WOp<T>& W, T& rho,
-                                       T& Fz, cpx<T>& Fp, unsigned* status) {
+                                       T& Fz, cpx<T>& Fp, unsigned* status, T* beta_out = nullptr) {
     T n[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) n[i] = norm2(psi[i]);
@@ -157,6 +157,7 @@ __device__ __forceinline__ int build_w(const cpx<T> psi[5], const PotConst<T>& C
     const T Fabs = sqrt(fma(Fz, Fz, norm2(Fp)));
     const T beta = fma(C.b1, Fabs, C.b2 * rho);
     if (!(beta <= T(kBetaMax))) atomicOr(status, 1u);
+    if (beta_out) *beta_out = beta;
     const int K = warp_taylor_degree(beta, TaylorTol<T>::value);
     const T g2r = C.dr * rho;
     const T gz = C.dz * Fz;
@@ -178,61 +179,138 @@ __device__ __forceinline__ int build_w(const cpx<T> psi[5], const PotConst<T>& C
     return K;
 }
 
+// FP64 pull-backs run the Horner steps of order above k0 in FP32 (Kin = K - k0 inner steps) and
+// the k0 outer ones in FP64, as the forward step does (zframe_inner_fp32), with k0 the smallest
+// order whose bound beta^k0 / k0! is at most kAdjInnerTol: smaller than the forward's 2^-31
+// because an error in the inner iterate of the lower recursion enters the Frechet terms once per
+// outer step, multiplied by the spin or rank-two matrix (a factor up to ~k0 / beta more).
+constexpr double kAdjInnerTol = 3.637978807091713e-12;  // 2^-38
+
+template <class U>
+__device__ __forceinline__ cpx<U> to_prec(cpx<double> z) { return {U(z.re), U(z.im)}; }
+
+template <class U>
+__device__ __forceinline__ WOp<U> wop_to(const WOp<double>& W) {
+    WOp<U> V;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        V.D[i] = U(W.D[i]);
+        V.u[i] = to_prec<U>(W.u[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) V.ep[i] = to_prec<U>(W.ep[i]);
+    V.R = U(W.R);
+    return V;
+}
+
+// One Horner step (1/k = ik) of trace_terms' four recursions.
+template <class U>
+__device__ __forceinline__ void trace_step(const WOp<U>& W, const cpx<U> x[5], cpx<U> v2[5], cpx<U> vx[5],
+                                           cpx<U> vy[5], cpx<U> vz[5], U ik) {
+    cpx<U> w[5], e[5];
+    W.apply(vx, w);
+    apply_fx(v2, e);
+    horner_upper(w, e, vx, ik, ik);
+    W.apply(vy, w);
+    apply_fy(v2, e);
+    horner_upper(w, e, vy, ik, ik);
+    W.apply(vz, w);
+    apply_fz(v2, e);
+    horner_upper(w, e, vz, ik, ik);
+    W.apply(v2, w);
+    horner_sgn(x, w, v2, ik);
+}
+
 // tr terms of one input vector x_r with its output cotangent g_r:
 //   tr_xyz[nu] += g_r^dagger L(B, f_nu) x_r,  tuc += g_r^dagger P(B) x_r
+// Wf: W in FP32, for the Kin inner steps of an FP64 call.
 template <class T>
-__device__ __forceinline__ void trace_terms(const WOp<T>& W, const cpx<T> x[5], const cpx<T> g[5], int K,
-                                            cpx<T> tr[3], cpx<T>& tuc) {
+__device__ __forceinline__ void trace_terms(const WOp<T>& W, const WOp<float>& Wf, const cpx<T> x[5],
+                                            const cpx<T> g[5], int K, int Kin, cpx<T> tr[3], cpx<T>& tuc) {
     cpx<T> v2[5], vx[5], vy[5], vz[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         v2[i] = x[i];
         vx[i] = vy[i] = vz[i] = {T(0), T(0)};
     }
-    for (int k = K; k >= 1; --k) {
-        const T ik = inv_k(k, T(0));
-        cpx<T> w[5], e[5];
-        W.apply(vx, w);
-        apply_fx(v2, e);
-        horner_upper(w, e, vx, ik, ik);
-        W.apply(vy, w);
-        apply_fy(v2, e);
-        horner_upper(w, e, vy, ik, ik);
-        W.apply(vz, w);
-        apply_fz(v2, e);
-        horner_upper(w, e, vz, ik, ik);
-        W.apply(v2, w);
-        horner_sgn(x, w, v2, ik);
+    int k = K;
+    if constexpr (std::is_same<T, double>::value) {
+        if (Kin > 0) {  // warp-uniform
+            cpx<float> xf[5], v2f[5], vxf[5], vyf[5], vzf[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                xf[i] = to_prec<float>(x[i]);
+                v2f[i] = xf[i];
+                vxf[i] = vyf[i] = vzf[i] = {0.f, 0.f};
+            }
+            for (; k > K - Kin; --k) trace_step<float>(Wf, xf, v2f, vxf, vyf, vzf, inv_k(k, 0.f));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                v2[i] = {double(v2f[i].re), double(v2f[i].im)};
+                vx[i] = {double(vxf[i].re), double(vxf[i].im)};
+                vy[i] = {double(vyf[i].re), double(vyf[i].im)};
+                vz[i] = {double(vzf[i].re), double(vzf[i].im)};
+            }
+        }
     }
+    for (; k >= 1; --k) trace_step<T>(W, x, v2, vx, vy, vz, inv_k(k, T(0)));
     tr[0] = tr[0] + cdot(g, vx);
     tr[1] = tr[1] + cdot(g, vy);
     tr[2] = tr[2] + cdot(g, vz);
     tuc = tuc + cdot(g, v2);
 }
 
+// One Horner step (1/k = ik) of frechet_rank2's two recursions.
+template <class U>
+__device__ __forceinline__ void frechet_step(const WOp<U>& W, const cpx<U> s[5], const cpx<U> p0[5],
+                                             const cpx<U> q0[5], const cpx<U> p1[5], const cpx<U> q1[5],
+                                             cpx<U> v2[5], cpx<U> out[5], U sgn, U ik) {
+    cpx<U> w[5], e[5];
+    const cpx<U> c0 = cdot(q0, v2), c1 = cdot(q1, v2);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) e[i] = cfma(c1, p1[i], cmul(c0, p0[i]));
+    W.apply(out, w);
+    horner_upper(w, e, out, sgn * ik, ik);
+    W.apply(v2, w);
+    horner_sgn(s, w, v2, sgn * ik);
+}
+
 // q = L(sgn B, E) s with E v = sum_r p_r (q_r^dagger v): for G s take (p, q) = (x, g) and
-// sgn = +1; for G^dagger s take (p, q) = (g, x) and sgn = -1.
+// sgn = +1; for G^dagger s take (p, q) = (g, x) and sgn = -1.  Wf, Kin as in trace_terms.
 template <class T>
-__device__ __forceinline__ void frechet_rank2(const WOp<T>& W, const cpx<T> s[5], const cpx<T> p0[5],
-                                              const cpx<T> q0[5], const cpx<T> p1[5], const cpx<T> q1[5],
-                                              int K, T sgn, cpx<T> out[5]) {
+__device__ __forceinline__ void frechet_rank2(const WOp<T>& W, const WOp<float>& Wf, const cpx<T> s[5],
+                                              const cpx<T> p0[5], const cpx<T> q0[5], const cpx<T> p1[5],
+                                              const cpx<T> q1[5], int K, int Kin, T sgn, cpx<T> out[5]) {
     cpx<T> v2[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         v2[i] = s[i];
         out[i] = {T(0), T(0)};
     }
-    for (int k = K; k >= 1; --k) {
-        const T ik = inv_k(k, T(0));
-        cpx<T> w[5], e[5];
-        const cpx<T> c0 = cdot(q0, v2), c1 = cdot(q1, v2);
+    int k = K;
+    if constexpr (std::is_same<T, double>::value) {
+        if (Kin > 0) {  // warp-uniform
+            cpx<float> sf[5], p0f[5], q0f[5], p1f[5], q1f[5], v2f[5], outf[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) e[i] = cfma(c1, p1[i], cmul(c0, p0[i]));
-        W.apply(out, w);
-        horner_upper(w, e, out, sgn * ik, ik);
-        W.apply(v2, w);
-        horner_sgn(s, w, v2, sgn * ik);
+            for (int i = 0; i < 5; ++i) {
+                sf[i] = to_prec<float>(s[i]);
+                p0f[i] = to_prec<float>(p0[i]);
+                q0f[i] = to_prec<float>(q0[i]);
+                p1f[i] = to_prec<float>(p1[i]);
+                q1f[i] = to_prec<float>(q1[i]);
+                v2f[i] = sf[i];
+                outf[i] = {0.f, 0.f};
+            }
+            for (; k > K - Kin; --k)
+                frechet_step<float>(Wf, sf, p0f, q0f, p1f, q1f, v2f, outf, float(sgn), inv_k(k, 0.f));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                v2[i] = {double(v2f[i].re), double(v2f[i].im)};
+                out[i] = {double(outf[i].re), double(outf[i].im)};
+            }
+        }
     }
+    for (; k >= 1; --k) frechet_step<T>(W, s, p0, q0, p1, q1, v2, out, sgn, inv_k(k, T(0)));
 }
 
 // Pull-back through U at one site.  (a, b): the state before U.  (ga, gb): cotangents of the
@@ -245,9 +323,16 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
 #pragma unroll
     for (int i = 0; i < 5; ++i) psi[i] = a[i] + b[i];
     WOp<T> W;
-    T rho, Fz;
+    T rho, Fz, beta;
     cpx<T> Fp;
-    const int K = build_w(psi, A.pc, W, rho, Fz, Fp, status);
+    const int K = build_w(psi, A.pc, W, rho, Fz, Fp, status, &beta);
+    int Kin = 0;  // FP64: inner Horner steps in FP32 (kAdjInnerTol)
+    WOp<float> Wf;
+    if constexpr (std::is_same<T, double>::value) {
+        const int k0 = warp_max_int(taylor_degree(beta, kAdjInnerTol) + 1);
+        Kin = K > k0 ? K - k0 : 0;
+        Wf = wop_to<float>(W);
+    }
     T sn, cs;
     sin_cos(A.pc.cphase * rho, &sn, &cs);
     const cpx<T> ph = {cs, -sn};  // e^{-i delta c}
@@ -255,8 +340,8 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
     // tau and phi_nu
     cpx<T> tr[3] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
     cpx<T> tuc = {T(0), T(0)};
-    trace_terms(W, a, ga, K, tr, tuc);
-    trace_terms(W, b, gb, K, tr, tuc);
+    trace_terms(W, Wf, a, ga, K, Kin, tr, tuc);
+    trace_terms(W, Wf, b, gb, K, Kin, tr, tuc);
     const T tau = cmul(ph, tuc).im;
     const T phx = cmul(ph, tr[0]).im, phy = cmul(ph, tr[1]).im, phz = cmul(ph, tr[2]).im;
 
@@ -265,8 +350,8 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
 #pragma unroll
     for (int i = 0; i < 5; ++i) s[i] = {W.u[i].re, -W.u[i].im};  // s = conj(u)
     cpx<T> q1[5], q2[5];
-    frechet_rank2(W, s, a, ga, b, gb, K, T(1), q1);
-    frechet_rank2(W, s, ga, a, gb, b, K, T(-1), q2);
+    frechet_rank2(W, Wf, s, a, ga, b, gb, K, Kin, T(1), q1);
+    frechet_rank2(W, Wf, s, ga, a, gb, b, K, Kin, T(-1), q2);
     cpx<T> Hs[5];
     const cpx<T> phc = {cs, sn};
 #pragma unroll
@@ -313,7 +398,31 @@ __device__ __forceinline__ void potential_vjp_site(const cpx<T> a[5], const cpx<
         pa[i] = ga[i];
         pb[i] = gb[i];
     }
-    for (int k = K; k >= 1; --k) {
+    int k = K;
+    if constexpr (std::is_same<T, double>::value) {
+        if (Kin > 0) {  // warp-uniform
+            cpx<float> gaf[5], gbf[5], paf[5], pbf[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                gaf[i] = paf[i] = to_prec<float>(ga[i]);
+                gbf[i] = pbf[i] = to_prec<float>(gb[i]);
+            }
+            for (; k > K - Kin; --k) {
+                const float ik = inv_k(k, 0.f);
+                cpx<float> wa[5], wb[5];
+                Wf.apply(paf, wa);
+                Wf.apply(pbf, wb);
+                horner_sgn(gaf, wa, paf, -ik);
+                horner_sgn(gbf, wb, pbf, -ik);
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                pa[i] = {double(paf[i].re), double(paf[i].im)};
+                pb[i] = {double(pbf[i].re), double(pbf[i].im)};
+            }
+        }
+    }
+    for (; k >= 1; --k) {
         const T ik = inv_k(k, T(0));
         cpx<T> wa[5], wb[5];
         W.apply(pa, wa);

@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "QLGA site-updates/s and % of HBM roofline (FP32 vs FP64, plain vs batched/adjoint)"
 UNIT = "site-updates/s"
 BYTES_PER_SITE_F32 = 160      # one read + one write of 10 complex FP32 amplitudes
+FIELDS_BYTES_PER_SITE_F32 = 80 + 44   # qlga_fields: one read of the true state, 11 FP32 values written
 
 
 def parse():
@@ -462,6 +463,28 @@ def run_paths(args, torch, qlga, inputs, state_f32, rate_fp32):
     sec = _timed_steps(torch, lat, 10)
     lat.close()
     out["interleaved_fp32_2d"] = {"lattice": [n, n], "site_updates_per_s": n * n / sec, "ms_per_step": sec * 1e3}
+    # per-site diagnostic fields of the bench lattice (F_par, F_perp, |A00|, colour map, vorticity
+    # of each level): one read of the true state (80 B per site in FP32) and 11 values written per
+    # site (44 B), on the device
+    lat = qlga.Lattice(2, n, n, precision=32, g=inputs.CONFIG2_G)
+    lat.load_state(state_f32)
+    fbuf = torch.empty(11 * n * n, dtype=torch.float32, device="cuda")
+    qlga.qlga_fields(lat.handle, fbuf.data_ptr(), qlga.QLGA_DEVICE)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    for _ in range(10):
+        qlga.qlga_fields(lat.handle, fbuf.data_ptr(), qlga.QLGA_DEVICE)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 10
+    lat.close()
+    del fbuf
+    peak, peak_kind = measured_peaks()
+    gbs = FIELDS_BYTES_PER_SITE_F32 * n * n / (ms * 1e-3) / 1e9
+    out["fields_fp32_2d"] = {"lattice": [n, n], "ms_per_call": ms, "sites_per_s": n * n / (ms * 1e-3),
+                             "algorithmic_bytes_per_site": FIELDS_BYTES_PER_SITE_F32, "achieved_gbs": gbs,
+                             "hbm_frac": gbs / peak, "peak_source": peak_kind,
+                             "accuracy": "against the oracle's fields in the GPU parity tests"}
     # batched 1D (256 runs, FP32, graph replay) against one FP64 run of the mean length
     bw = inputs.config3()
     b = qlga.Batch1D(bw.lengths, bw.couplings, precision=32)

@@ -216,9 +216,11 @@ qlga_status qlga_objective(qlga_handle* h, const void* x_device, int32_t level, 
  *   2 |A00| = |psi^T J psi| / sqrt(5)   3..5 (r, g, b) = (|F_par|, F_perp, |A00|) / their norm
  *                                           (0 where all three vanish)
  *   6..10 vorticity of level m = +2..-2: phase S = arg psi_m, v = wrapped central differences
- *         of S / 2, vorticity = central-difference curl of v (0 in 1D).
- * Phases are taken in FP64 for both precisions.  `where` is QLGA_HOST or QLGA_DEVICE; a host
- * copy waits for the stream. */
+ *         of S / 2, vorticity = central-difference curl of v (0 in 1D).  The unwrapped parts of
+ *         the four differences cancel, so the value is pi/2 times an integer, the sum of their
+ *         wrap counts; the counts are those of the FP64 phases in both precisions (phases near a
+ *         wrap decision are taken again in FP64).
+ * `where` is QLGA_HOST or QLGA_DEVICE; a host copy waits for the stream. */
 qlga_status qlga_fields(qlga_handle* h, void* dst, int where);
 
 /* Observables of a caller-provided device state without allocating any device memory.

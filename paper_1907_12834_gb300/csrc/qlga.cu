@@ -381,6 +381,7 @@ __device__ __forceinline__ double wrap_pi(double d) {
     return d > pi ? d - 2.0 * pi : (d <= -pi ? d + 2.0 * pi : d);
 }
 
+// One site per thread; qlga_fields takes it for 1D lattices (2D lattices: k_fields2d below).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T* __restrict__ out,
                                                      int64_t nx, int64_t ny, int ndim) {

@@ -127,8 +127,8 @@ __device__ __forceinline__ void put_pq(float* X, int64_t pair, cpx<float> a, cpx
 
 // U on every site, in place.  All lanes of a warp run the potential (the Taylor degree is a
 // warp-wide maximum); lanes past the end work on zeros and store nothing.
-// HELD_PQ: store the result as (P, Q) = (a + bt, a - bt), the form in which the fused 2D steps
-// hold a state pending K (qlga_step2d.cuh); else in the resident layout (a, bt).
+// HELD_PQ: store the result as (P, Q) = (a + bt, a - bt), the form in which 1D lattices and the
+// fused 2D steps hold a state pending K (qlga_step2d.cuh); else in the resident layout (a, bt).
 template <class T, bool SPLIT, bool HELD_PQ = false>
 __global__ void __launch_bounds__(kThreads) k_potential(T* X, int64_t nsites, PotConst<T> PC,
                                                         unsigned* status) {

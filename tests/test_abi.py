@@ -142,3 +142,37 @@ def test_buffer_checks_of_the_binding():
         qlga.require_host_array(ro, shape, np.float32, "x", writable=True)
     with pytest.raises(TypeError):
         qlga.require_device_tensor(torch.zeros(shape), shape, torch.float32, torch.device("cuda", 0), "x")
+
+
+def test_obs_from_sums_forms_the_observables(lib):
+    """qlga_obs_from_sums (host only) against the oracle's observables of a random 2D state: the 14
+    sums in the ABI's order go in, the magnetisation sum_m m pop[m] and the singlet fraction
+    sum |psi^T J psi|^2 / sum rho^2 come out as the oracle forms them (Sec. III.B Eq. cmap)."""
+    import numpy as np
+    import oracle
+    from paper_1907_12834_gb300 import inputs
+
+    rng = np.random.default_rng(77)
+    nx, ny = 12, 9
+    st = np.ascontiguousarray(inputs.random_state(rng, nx, ny, scale=0.2), dtype=np.float64)
+    ref = np.ascontiguousarray(inputs.random_state(rng, nx, ny, scale=0.2), dtype=np.float64)
+    o = oracle.observables(st, oracle.make_cfg(2, nx, ny, 1.0, 0.8, -0.6), ref=ref)
+    sums = np.array([o["norm_qubit"], o["norm_boson"], *o["pop"], o["energy"], o["singlet_re"],
+                     o["singlet_im"], o["theta2_sum"], o["rho2_sum"], o["overlap_re"], o["overlap_im"]])
+    d = qlga.obs_to_dict(qlga.qlga_obs_from_sums(sums, 17))
+    assert d["step"] == 17
+    assert abs(d["magnetisation"] - o["magnetisation"]) <= 1e-13 * o["norm_qubit"]
+    assert d["singlet_fraction"] == pytest.approx(o["singlet_fraction"], rel=1e-15)
+    for k in ("norm_qubit", "norm_boson", "energy", "singlet_re", "singlet_im", "overlap_re", "overlap_im"):
+        assert d[k] == o[k]
+    np.testing.assert_array_equal(d["pop"], o["pop"])
+    # an all-zero field has no singlet fraction to form: 0, not a division by zero
+    assert qlga.obs_to_dict(qlga.qlga_obs_from_sums(np.zeros(14)))["singlet_fraction"] == 0.0
+    bad = sums.copy()
+    bad[7] = float("nan")                     # the energy
+    with pytest.raises(qlga.QlgaError) as ei:
+        qlga.qlga_obs_from_sums(bad)
+    assert ei.value.status == qlga.QLGA_ERR_NOT_FINITE
+    assert lib.qlga_obs_from_sums(None, 0, None) == qlga.QLGA_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        qlga.qlga_obs_from_sums(sums[:13])

@@ -347,7 +347,7 @@ __device__ __forceinline__ int warp_taylor_degree(T beta, T tol) {
 // y = (delta W) x, with the per-site coefficients of W
 template <class T>
 struct WOp {
-    T D[5];        // diagonal: delta (g1 F_z m - g2 rho / 25)
+    T D[5];        // diagonal: delta (g1 F_z m - g2 rho / 10)
     cpx<T> ep[4];  // (i+1, i) entries: delta g1 c_i F_+ ; (i, i+1) = conj
     cpx<T> u[5];   // u_j = (-1)^{m_j} psi_{4-j} = conj(s_j)
     T R;           // delta g2 / 5 (times inv_sigma2)

@@ -560,6 +560,34 @@ def test_fields(precision, ndim):
     np.testing.assert_allclose(got[6:], ref[6:], rtol=0, atol=1e-9 if precision == 64 else 1e-6)
 
 
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("nx,ny", [(72, 21), (40, 9), (8, 8)])
+def test_fields_ragged_tiles(precision, nx, ny):
+    """The tiled 2D fields kernel (tiles of 32 x 8 sites with a periodic one-site halo) on lattices
+    that end inside a tile or are smaller than one, with random phases everywhere, so that many
+    wrap counts are nonzero and some phase differences come close to +-pi."""
+    rng = np.random.default_rng(nx * ny + precision)
+    g = (1.0, 0.8, -0.6)
+    st = I.random_state(rng, nx, ny, scale=0.1)
+    lat = qlga.Lattice(2, nx, ny, precision=precision, g=g)
+    lat.load_state(st.astype(np.float32 if precision == 32 else np.float64))
+    lat.step(2)
+    got = lat.fields()
+    cur = lat.get_state()
+    lat.close()
+    ref = oracle.fields(np.ascontiguousarray(cur, dtype=np.float64), oracle.make_cfg(2, nx, ny, *g))
+    tol = 1e-12 if precision == 64 else 2e-5
+    scale = np.abs(ref[:3]).max()
+    np.testing.assert_allclose(got[:3], ref[:3], rtol=0, atol=tol * scale)
+    mask = np.sqrt((ref[:3] ** 2).sum(0)) > 1e-6 * scale
+    np.testing.assert_allclose(got[3:6][:, mask], ref[3:6][:, mask], rtol=0,
+                               atol=(1e-12 if precision == 64 else 1e-4))
+    np.testing.assert_allclose(got[6:], ref[6:], rtol=0, atol=1e-9 if precision == 64 else 1e-6)
+    counts = got[6:].astype(np.float64) / (np.pi / 2)
+    np.testing.assert_allclose(counts, np.round(counts), rtol=0, atol=1e-6)
+    assert np.count_nonzero(np.round(counts)) > 0
+
+
 @pytest.mark.parametrize("ndim,nx,ny,precision", [(1, 1024, 1, 64), (1, 16384, 1, 32), (2, 128, 64, 32),
                                                   (2, 40, 24, 64)])
 def test_step_graphs_give_identical_results(ndim, nx, ny, precision):

@@ -440,25 +440,71 @@ __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T*
 // tile and its one-site periodic halo are computed once into shared memory (each site's phase
 // serves the four sites whose diagonal neighbour it is: 1.3 phases per site and level instead of
 // 4), with the FP32 atan2 of psi = a + b formed in FP64 and rounded once (within a few 1e-7 rad;
-// the FP64 atan2 costs 60 times more on GB300).  The four phase differences of the vorticity
+// the FP64 atan2 costs 60 times more on GB300).  Each thread reads its own site once: its phases
+// fill the tile's interior and its local fields are written before the block's barrier; the first
+// kFieldsRing threads read the ring of halo sites.  The kernel waits mostly on its loads, so it
+// runs five blocks per SM (48 registers, a few bytes spilled) rather than the four that the 60
+// registers the compiler picks alone allow.  The four phase differences of the vorticity
 // cancel but for their wraps, so it is pi/2 times an integer, the sum of the wrap counts; a count
 // is the one place where the phase error could change a result, and a site and level where one of
 // its four differences lies within 1e-4 of +-pi takes its four phases again in FP64, so every
 // count is the FP64 one and the vorticity is (pi/2) N exactly in either precision.
 constexpr int kFieldsTx = 32, kFieldsTy = 8;
+constexpr int kFieldsRing = 2 * (kFieldsTx + 2) + 2 * kFieldsTy;  // halo sites around a tile: 84
+static_assert(kFieldsRing <= kFieldsTx * kFieldsTy, "one ring site per thread at most");
 template <class T>
-__global__ void __launch_bounds__(kFieldsTx * kFieldsTy) k_fields2d(const T* __restrict__ X, T* __restrict__ out,
+__global__ void __launch_bounds__(kFieldsTx * kFieldsTy, 5) k_fields2d(const T* __restrict__ X, T* __restrict__ out,
                                                                     int64_t nx, int64_t ny) {
     __shared__ float ph[5][kFieldsTy + 2][kFieldsTx + 2];
     const int64_t nsites = nx * ny;
     const T r32 = T(1.2247448713915890491);
     const int64_t tiles_x = (nx + kFieldsTx - 1) / kFieldsTx, tiles_y = (ny + kFieldsTy - 1) / kFieldsTy;
     const int tx = threadIdx.x % kFieldsTx, ty = threadIdx.x / kFieldsTx;
+    // the ring entry (hy, hx) of this thread's halo site, for threads below kFieldsRing: the top
+    // and bottom rows of the halo box, then its left and right columns
+    const int r = threadIdx.x;
+    const int ring_hy = r < kFieldsTx + 2 ? 0
+                        : r < 2 * (kFieldsTx + 2) ? kFieldsTy + 1
+                        : 1 + (r - 2 * (kFieldsTx + 2)) % kFieldsTy;
+    const int ring_hx = r < kFieldsTx + 2 ? r
+                        : r < 2 * (kFieldsTx + 2) ? r - (kFieldsTx + 2)
+                        : (r < 2 * (kFieldsTx + 2) + kFieldsTy ? 0 : kFieldsTx + 1);
     for (int64_t tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
         const int64_t x0 = (tile % tiles_x) * kFieldsTx, y0 = (tile / tiles_x) * kFieldsTy;
-        for (int i = threadIdx.x; i < (kFieldsTx + 2) * (kFieldsTy + 2); i += blockDim.x) {
-            const int hx = i % (kFieldsTx + 2), hy = i / (kFieldsTx + 2);
-            int64_t xx = (x0 - 1 + hx) % nx, yy = (y0 - 1 + hy) % ny;
+        const int64_t x = x0 + tx, y = y0 + ty;
+        const bool inside = x < nx && y < ny;
+        {
+            // this thread's site, or its periodic image where the tile passes the lattice's edge
+            const int64_t site = (y % ny) * nx + (x % nx);
+            cpx<T> psi[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                cpx<T> a, b;
+                load_pair<T>(X, nsites, m, site, a, b);
+                psi[m] = a + b;
+                const double re = double(a.re) + double(b.re), im = double(a.im) + double(b.im);
+                ph[m][ty + 1][tx + 1] = atan2f(float(im), float(re));
+            }
+            if (inside) {
+                const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
+                cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
+                const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
+                Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
+                const T fperp = sqrt(norm2(Fp));
+                const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
+                const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
+                const T a00 = sqrt(norm2(th)) * T(0.44721359549995793928);
+                const T nrm = sqrt(Fz * Fz + fperp * fperp + a00 * a00);
+                out[0 * nsites + site] = Fz;
+                out[1 * nsites + site] = fperp;
+                out[2 * nsites + site] = a00;
+                out[3 * nsites + site] = nrm > T(0) ? fabs(Fz) / nrm : T(0);
+                out[4 * nsites + site] = nrm > T(0) ? fperp / nrm : T(0);
+                out[5 * nsites + site] = nrm > T(0) ? a00 / nrm : T(0);
+            }
+        }
+        if (r < kFieldsRing) {
+            int64_t xx = (x0 - 1 + ring_hx) % nx, yy = (y0 - 1 + ring_hy) % ny;
             xx = xx < 0 ? xx + nx : xx;
             yy = yy < 0 ? yy + ny : yy;
 #pragma unroll
@@ -466,35 +512,12 @@ __global__ void __launch_bounds__(kFieldsTx * kFieldsTy) k_fields2d(const T* __r
                 cpx<T> a, b;
                 load_pair<T>(X, nsites, m, yy * nx + xx, a, b);
                 const double re = double(a.re) + double(b.re), im = double(a.im) + double(b.im);
-                ph[m][hy][hx] = atan2f(float(im), float(re));
+                ph[m][ring_hy][ring_hx] = atan2f(float(im), float(re));
             }
         }
         __syncthreads();
-        const int64_t x = x0 + tx, y = y0 + ty;
-        if (x < nx && y < ny) {
+        if (inside) {
             const int64_t site = y * nx + x;
-            cpx<T> psi[5];
-#pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                cpx<T> a, b;
-                load_pair<T>(X, nsites, m, site, a, b);
-                psi[m] = a + b;
-            }
-            const T Fz = T(2) * (norm2(psi[0]) - norm2(psi[4])) + (norm2(psi[1]) - norm2(psi[3]));
-            cpx<T> Fp = cmulc(psi[0], psi[1]) + cmulc(psi[3], psi[4]);
-            const cpx<T> mid = cmulc(psi[1], psi[2]) + cmulc(psi[2], psi[3]);
-            Fp = {T(2) * (Fp.re + r32 * mid.re), T(2) * (Fp.im + r32 * mid.im)};
-            const T fperp = sqrt(norm2(Fp));
-            const cpx<T> t1 = cmul(psi[0], psi[4]), t2 = cmul(psi[1], psi[3]), t3 = cmul(psi[2], psi[2]);
-            const cpx<T> th = {T(2) * (t1.re - t2.re) + t3.re, T(2) * (t1.im - t2.im) + t3.im};
-            const T a00 = sqrt(norm2(th)) * T(0.44721359549995793928);
-            const T nrm = sqrt(Fz * Fz + fperp * fperp + a00 * a00);
-            out[0 * nsites + site] = Fz;
-            out[1 * nsites + site] = fperp;
-            out[2 * nsites + site] = a00;
-            out[3 * nsites + site] = nrm > T(0) ? fabs(Fz) / nrm : T(0);
-            out[4 * nsites + site] = nrm > T(0) ? fperp / nrm : T(0);
-            out[5 * nsites + site] = nrm > T(0) ? a00 / nrm : T(0);
             const int64_t xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
             const int64_t yp = y + 1 == ny ? 0 : y + 1, ym = y == 0 ? ny - 1 : y - 1;
 #pragma unroll
@@ -1949,7 +1972,14 @@ qlga_status qlga_fields(qlga_handle* h, void* dst, int where) {
     if (where == QLGA_HOST) target = (view == h->tmp) ? h->X[1 - h->cur] : h->tmp;
     if (h->cfg.ndim == 2) {
         const int64_t tiles = ((h->cfg.nx + kFieldsTx - 1) / kFieldsTx) * ((h->cfg.ny + kFieldsTy - 1) / kFieldsTy);
-        const int64_t cap = 8 * int64_t(device_sms());
+        // one wave of resident blocks: each block loops over tiles, so blocks beyond the resident
+        // count would start only when the first wave has finished all of its tiles
+        int per_sm = 0;
+        QLGA_CUDA(h->cfg.precision == 32
+                      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fields2d<float>, kFieldsTx * kFieldsTy, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fields2d<double>, kFieldsTx * kFieldsTy, 0),
+                  "k_fields2d occupancy");
+        const int64_t cap = int64_t(per_sm > 0 ? per_sm : 1) * device_sms();
         const int grid = int(tiles < cap ? tiles : cap);
         if (h->cfg.precision == 32)
             k_fields2d<float><<<grid, kFieldsTx * kFieldsTy, 0, h->stream>>>(static_cast<const float*>(view), static_cast<float*>(target), h->cfg.nx, h->cfg.ny);

@@ -444,7 +444,8 @@ __global__ void __launch_bounds__(kThreads) k_fields(const T* __restrict__ X, T*
 // fill the tile's interior and its local fields are written before the block's barrier; the first
 // kFieldsRing threads read the ring of halo sites.  The kernel waits mostly on its loads, so it
 // runs five blocks per SM (48 registers, a few bytes spilled) rather than the four that the 60
-// registers the compiler picks alone allow.  The four phase differences of the vorticity
+// registers the compiler picks alone allow; consecutive tiles fill alternate phase buffers, so one
+// barrier per tile suffices.  The four phase differences of the vorticity
 // cancel but for their wraps, so it is pi/2 times an integer, the sum of the wrap counts; a count
 // is the one place where the phase error could change a result, and a site and level where one of
 // its four differences lies within 1e-4 of +-pi takes its four phases again in FP64, so every
@@ -455,7 +456,8 @@ static_assert(kFieldsRing <= kFieldsTx * kFieldsTy, "one ring site per thread at
 template <class T>
 __global__ void __launch_bounds__(kFieldsTx * kFieldsTy, 5) k_fields2d(const T* __restrict__ X, T* __restrict__ out,
                                                                     int64_t nx, int64_t ny) {
-    __shared__ float ph[5][kFieldsTy + 2][kFieldsTx + 2];
+    __shared__ float phb[2][5][kFieldsTy + 2][kFieldsTx + 2];
+    int parity = 0;
     const int64_t nsites = nx * ny;
     const T r32 = T(1.2247448713915890491);
     const int64_t tiles_x = (nx + kFieldsTx - 1) / kFieldsTx, tiles_y = (ny + kFieldsTy - 1) / kFieldsTy;
@@ -470,6 +472,7 @@ __global__ void __launch_bounds__(kFieldsTx * kFieldsTy, 5) k_fields2d(const T* 
                         : r < 2 * (kFieldsTx + 2) ? r - (kFieldsTx + 2)
                         : (r < 2 * (kFieldsTx + 2) + kFieldsTy ? 0 : kFieldsTx + 1);
     for (int64_t tile = blockIdx.x; tile < tiles_x * tiles_y; tile += gridDim.x) {
+        float (*ph)[kFieldsTy + 2][kFieldsTx + 2] = phb[parity];
         const int64_t x0 = (tile % tiles_x) * kFieldsTx, y0 = (tile / tiles_x) * kFieldsTy;
         const int64_t x = x0 + tx, y = y0 + ty;
         const bool inside = x < nx && y < ny;
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(kFieldsTx * kFieldsTy, 5) k_fields2d(const T* 
                 else out[(6 + m) * nsites + site] = 1.5707963267948966 * double(N);
             }
         }
-        __syncthreads();  // the next tile reuses ph
+        parity ^= 1;  // the next tile fills the other buffer: one barrier per tile
     }
 }
 

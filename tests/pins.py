@@ -275,6 +275,66 @@ def pin_norm(orc, ndim=2, nsteps=4):
     return abs(float((st ** 2).sum()) - n0) / n0
 
 
+# ----------------------------------------------------------------- observables
+
+def _uniform_state(c, nx, ny):
+    """a = b = c / 2 on every site of an nx x ny lattice (c complex, 5 levels)."""
+    st = np.zeros((5, ny, nx, 2, 2))
+    for q in (0, 1):
+        st[..., q, 0] = (np.real(c) / 2)[:, None, None]
+        st[..., q, 1] = (np.imag(c) / 2)[:, None, None]
+    return st
+
+
+def pin_observables(orc):
+    """Observables against closed forms (Sec. III.B Eq. cmap, Sec. IV.B).  Uniform Thomas-Fermi
+    rows (Table I) turned by a global phase phi: the energy density is E rho / 2 (c^dagger V(c) c
+    = E rho for an eigenvector of V), the qubit populations |c_m|^2 / 2, the magnetisation
+    sum_m m |c_m|^2 / 2, the qubit norm rho / 2 per site, and the overlap with the same state
+    turned by alpha is N rho e^{i alpha}; row 5 (m = 0 only) has the singlet sum
+    N c_0^2 e^{2 i phi} / sqrt(5) and singlet fraction 1, row 1 (m = +2 only) neither.  Plane
+    waves A e^{i k x} along x and along y carry the forward-difference kinetic energy
+    2 |A|^2 (1 - cos k) per site."""
+    worst = 0.0
+    E, g0, g1, g2 = 0.02, 1.0, 0.1, 1.0
+    nx, ny = 4, 3
+    N = nx * ny
+    phi, alpha = 0.7, -1.1
+    ms = np.array([2.0, 1.0, 0.0, -1.0, -2.0])
+    for row, c in golden.table1(E, g0, g1, g2, c1=0.03, c2=0.02).items():
+        c = np.asarray(c, dtype=float) * np.exp(1j * phi)
+        st = _uniform_state(c, nx, ny)
+        ref = _uniform_state(c * np.exp(1j * alpha), nx, ny)
+        o = orc.observables(st, oracle.make_cfg(2, nx, ny, g0, g1, g2), ref=ref)
+        p = np.abs(c) ** 2
+        rho = float(p.sum())
+        dev = [o["energy"] - N * E * rho / 2, o["magnetisation"] - N * float(ms @ p) / 2,
+               o["norm_boson"] - N * rho, o["norm_qubit"] - N * rho / 2,
+               complex(o["overlap_re"], o["overlap_im"]) - N * rho * np.exp(1j * alpha)]
+        dev += list(o["pop"] - N * p / 2)
+        if row == 5:
+            dev += [complex(o["singlet_re"], o["singlet_im"]) - N * c[2] ** 2 / np.sqrt(5),
+                    o["singlet_fraction"] - 1.0]
+        if row == 1:
+            dev += [complex(o["singlet_re"], o["singlet_im"]), o["singlet_fraction"]]
+        worst = max(worst, max(abs(d) for d in dev))
+    # plane waves in level +1, along x and along y
+    nx, ny = 16, 8
+    A = 0.3 + 0.1j
+    for axis, n_axis in ((0, nx), (1, ny)):
+        k = 2 * np.pi * 3 / n_axis
+        j = np.arange(n_axis)
+        w = A * np.exp(1j * k * j) / 2
+        grid = w[None, :] * np.ones((ny, 1)) if axis == 0 else w[:, None] * np.ones((1, nx))
+        st = np.zeros((5, ny, nx, 2, 2))
+        for q in (0, 1):
+            st[1, ..., q, 0] = grid.real
+            st[1, ..., q, 1] = grid.imag
+        o = orc.observables(st, oracle.make_cfg(2, nx, ny, 0, 0, 0))
+        worst = max(worst, abs(o["energy"] - nx * ny * 2 * abs(A) ** 2 * (1 - np.cos(k))))
+    return worst
+
+
 # ----------------------------------------------------------------- per-site fields
 
 def pin_fields(orc):

@@ -54,6 +54,22 @@ MUTATIONS = [
      lambda o: pins.pin_vjp_fd(o, "potential"), 1e-8),
     ("coupling_g2_fifth", "dcoup[2] += delta * creal(sHs) / 5.0;", "dcoup[2] += delta * creal(sHs);",
      lambda o: pins.pin_coupling_fd(o), 1e-7),
+    # observables and per-site fields
+    ("energy_spin_term_full", "0.5 * cfg->g1 * F2", "cfg->g1 * F2", lambda o: pins.pin_observables(o), 1e-12),
+    ("energy_singlet_fifth", "0.1 * cfg->g2 * th2", "0.2 * cfg->g2 * th2", lambda o: pins.pin_observables(o), 1e-12),
+    ("energy_gradient_x_only", "for (int axis = 0; axis < cfg->ndim; ++axis) {\n                const long xn",
+     "for (int axis = 0; axis < 1; ++axis) {\n                const long xn", lambda o: pins.pin_observables(o), 1e-12),
+    ("singlet_without_sqrt5", "out[9] += creal(theta) / sqrt(5.0);", "out[9] += creal(theta);",
+     lambda o: pins.pin_observables(o), 1e-12),
+    ("magnetisation_sign", "out[7] += (2 - m) * pm;", "out[7] += (m - 2) * pm;", lambda o: pins.pin_observables(o), 1e-12),
+    ("overlap_unconjugated", "const cplx ov = conj(psi[m]) * r;", "const cplx ov = psi[m] * r;",
+     lambda o: pins.pin_observables(o), 1e-12),
+    ("a00_without_sqrt5", "const double a00 = cabs(theta) / sqrt(5.0);", "const double a00 = cabs(theta);",
+     lambda o: pins.pin_fields(o), 1e-12),
+    ("fperp_with_fz", "fperp = sqrt(F[0] * F[0] + F[1] * F[1]);", "fperp = sqrt(F[0] * F[0] + F[2] * F[2]);",
+     lambda o: pins.pin_fields(o), 1e-12),
+    ("colour_unnormalised", "out[3 * n + site] = nrm > 0 ? fabs(fpar) / nrm : 0.0;",
+     "out[3 * n + site] = nrm > 0 ? fabs(fpar) : 0.0;", lambda o: pins.pin_fields(o), 1e-12),
 ]
 
 

@@ -131,6 +131,11 @@ def test_observables_closed_forms(orc):
             assert abs(o["singlet_fraction"] - 1.0) < 1e-12
 
 
+def test_observables_pin(orc):
+    """The closed forms of pins.pin_observables (also used by the mutation tests)."""
+    assert pins.pin_observables(orc) < 1e-12
+
+
 def test_observables_plane_wave_gradient(orc):
     """Forward-difference kinetic energy of A e^{i k x}: 2 |A|^2 (1 - cos k) per site."""
     nx, ny = 16, 4
